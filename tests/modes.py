@@ -1,0 +1,36 @@
+"""Closed-form normal modes used as pins (scipy Bessel functions; test infrastructure).
+
+Annulus a < r < R with a rigid inner wall (dP/dr = 0 at r = a) and a Dirichlet outer wall
+(P = 0 at r = R): P = R_m(k r) cos(m theta) cos(omega t), omega = c k, where
+R_m(k r) = J_m(k r) Y_m'(k a) - Y_m(k r) J_m'(k a) and k solves R_m(k R) = 0
+(separation of variables of the wave equation in cylindrical coordinates, as in the
+paper's appendix "Radial modes of the pipe").
+"""
+import numpy as np
+from scipy.optimize import brentq
+from scipy.special import jv, jvp, yv, yvp
+
+
+def roots(fun, lo, hi, n_grid=20000):
+    xs = np.linspace(lo, hi, n_grid)
+    v = fun(xs)
+    out = []
+    for i in range(n_grid - 1):
+        if np.isfinite(v[i]) and np.isfinite(v[i + 1]) and v[i] * v[i + 1] < 0:
+            out.append(brentq(fun, xs[i], xs[i + 1], xtol=1e-14))
+    return out
+
+
+def annulus_radial(m, k, a, r):
+    return jv(m, k * r) * yvp(m, k * a) - yv(m, k * r) * jvp(m, k * a)
+
+
+def annulus_wavenumbers(m, a, R, count=3):
+    f = lambda k: annulus_radial(m, k, a, R)
+    ks = roots(f, 1e-4 / R, 40.0 / R)
+    return ks[:count]
+
+
+def pipe_zeros(m, count=3):
+    f = lambda x: (m + 1) * jv(m, x) - x * jv(m + 1, x)
+    return roots(f, 1e-3, 30.0)[:count]

@@ -1,0 +1,437 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test cites what fixes the expected value: the paper's coordinate maps (metric from the
+embedding), differential-geometry identities, the wave speed of the continuum equation,
+Bessel closed forms, a finite-difference solve of the paper's target equation (Eq. waves),
+linear algebra of the step operator, and synthetic sinusoids for the spectrum estimator.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from lbw_workloads import (BC_ANTIBOUNCE, BC_BOUNCE, BC_PERIODIC, KIND_CARTESIAN,
+                           KIND_CYLINDRICAL, KIND_POLAR, KIND_TOROIDAL, KIND_TRUMPET,
+                           PROFILE_BESSEL, PROFILE_EXP, GridSpec, embedding)
+from modes import annulus_radial, annulus_wavenumbers, pipe_zeros
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+W = lambda cs2: np.array([1 - 3 * cs2] + [cs2 / 2] * 6)
+
+
+def state_from_rho(rho, cs2=0.25):
+    """Post-collision populations f^eq(rho, 0) for an arbitrary rho field (N3, N1, N2)."""
+    return W(cs2)[:, None, None, None] * rho[None]
+
+
+# ---------------------------------------------------------------- geometry ----------------
+
+def _num_metric(spec, u, eps=1e-5):
+    """g_ab = J^T J from a central-difference Jacobian of the test's own embedding."""
+    J = np.zeros((3, 3))
+    for b in range(3):
+        du = np.zeros(3)
+        du[b] = eps
+        J[:, b] = (embedding(spec, *(u + du)) - embedding(spec, *(u - du))) / (2 * eps)
+    return J.T @ J
+
+
+def _num_geometry(spec, u):
+    g = _num_metric(spec, u)
+    return math.sqrt(np.linalg.det(g)), np.linalg.inv(g)
+
+
+GEOMS = [
+    GridSpec(kind=KIND_CARTESIAN, n=(4, 4, 4), h=(1, 1, 1), x0=(0, 0, 0), c=0.4),
+    GridSpec(kind=KIND_CYLINDRICAL, n=(4, 4, 4), h=(1, 1, 1), x0=(3, 0, 0), c=0.4),
+    GridSpec(kind=KIND_TRUMPET, n=(4, 4, 4), h=(1, 1, 1), x0=(3, 0, 0), c=0.4,
+             geom=(60.0, 0.2, 0, 0), profile=PROFILE_BESSEL),
+    GridSpec(kind=KIND_TRUMPET, n=(4, 4, 4), h=(1, 1, 1), x0=(3, 0, 0), c=0.4,
+             geom=(20.0, 4.0, 0.05, 0), profile=PROFILE_EXP),
+    GridSpec(kind=KIND_TOROIDAL, n=(4, 4, 4), h=(1, 1, 1), x0=(3, 0, 0), c=0.4,
+             geom=(12.0, 0, 0, 0)),
+]
+
+
+@pytest.mark.parametrize("spec", GEOMS, ids=["cart", "cyl", "bessel", "exp", "torus"])
+def test_metric_matches_embedding(spec):
+    """sqrt(g) and g^{ab} of the oracle equal det / inverse of J^T J of the coordinate map
+    (Eqs. cylindricalsystem, coordinatesTrumpet, CoordinatesTorus)."""
+    g = oracle.OracleGrid(spec)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        u = np.array([rng.uniform(3, 9), rng.uniform(0, 6.2), rng.uniform(0.5, 6.0)])
+        out = g.geometry(*u)
+        sg, gi = _num_geometry(spec, u)
+        assert out[0] == pytest.approx(sg, rel=1e-7)
+        got = np.array([[out[1], out[4], out[5]], [out[4], out[2], out[6]],
+                        [out[5], out[6], out[3]]])
+        np.testing.assert_allclose(got, gi, rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("spec", GEOMS, ids=["cart", "cyl", "bessel", "exp", "torus"])
+def test_contracted_christoffel_identity(spec):
+    """G^a = g^{bc} Gamma^a_{bc} = -(1/sqrt g) d_b (sqrt g g^{ab}) (a divergence identity),
+    with sqrt g, g^{ab} from the embedding and d_b by central differences."""
+    g = oracle.OracleGrid(spec)
+    rng = np.random.default_rng(1)
+    eps = 1e-3
+    for _ in range(10):
+        u = np.array([rng.uniform(3, 9), rng.uniform(0, 6.2), rng.uniform(0.5, 6.0)])
+        G = np.zeros(3)
+        for b in range(3):
+            du = np.zeros(3)
+            du[b] = eps
+            sp, gp = _num_geometry(spec, u + du)
+            sm, gm = _num_geometry(spec, u - du)
+            G -= (sp * gp[:, b] - sm * gm[:, b]) / (2 * eps)
+        G /= _num_geometry(spec, u)[0]
+        np.testing.assert_allclose(g.geometry(*u)[7:10], G, rtol=1e-4, atol=1e-6)
+
+
+def test_paper_christoffels_cylinder_and_torus():
+    """Contracting the paper's printed symbols: cylinder (Eq. CylindricalChr)
+    G^r = g^{theta theta} Gamma^r_{theta theta} = -1/r; torus (Eq. AChristoffelTorus with the
+    sign of Gamma^r_{theta theta} corrected to -(R + r cos phi) cos phi):
+    G^r = g^{tt} Gamma^r_tt + g^{pp} Gamma^r_pp, G^phi = g^{tt} Gamma^phi_tt."""
+    cyl = oracle.OracleGrid(GEOMS[1])
+    assert cyl.geometry(5.0, 1.0, 2.0)[7] == pytest.approx(-1 / 5.0)
+    tor = oracle.OracleGrid(GEOMS[4])
+    R, r, phi = 12.0, 5.0, 0.7
+    Rr = R + r * math.cos(phi)
+    Gr = (1 / Rr**2) * (-Rr * math.cos(phi)) + (1 / r**2) * (-r)
+    Gphi = (1 / Rr**2) * (Rr * math.sin(phi) / r)
+    out = tor.geometry(r, 0.3, phi)
+    assert out[7] == pytest.approx(Gr, rel=1e-12)
+    assert out[9] == pytest.approx(Gphi, rel=1e-12)
+
+
+# ---------------------------------------------------------------- flat space --------------
+
+def _plane_wave_omega(c, N, axis, cs2=0.25, steps=4000):
+    n = [1, 1, 1]
+    n[axis] = N
+    spec = GridSpec(kind=KIND_CARTESIAN, n=tuple(n), h=(1, 1, 1), x0=(0, 0, 0), c=c, cs2=cs2)
+    g = oracle.OracleGrid(spec)
+    k = 2 * math.pi / N
+    x = np.arange(N) + 0.5
+    shape = {0: (1, N, 1), 1: (1, 1, N), 2: (N, 1, 1)}[axis]  # state is (N3, N1, N2)
+    rho = np.cos(k * x).reshape(shape)
+    g.set_f(state_from_rho(rho, cs2))
+    g.set_probes([[0, 0, 0]], steps)
+    g.step(steps)
+    fr, am = oracle.spectrum(g.read_probes()[0], 2)
+    return fr[np.argmax(am)], c * k
+
+
+@pytest.mark.parametrize("c", [0.3, 0.7])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_flat_space_wave_speed(c, axis):
+    """Identity metric: P obeys P_tt = c^2 Lap P (Eq. waveEuclidean), so a long plane wave
+    oscillates at omega = c k.  With c != cs this fixes the sign and the cs^2 of the moved
+    divergence term (the printed +c^2 (g - delta) form gives speed^2 = 2 cs^2 - c^2)."""
+    om, ck = _plane_wave_omega(c, 64, axis)
+    assert abs(om / ck - 1) < 3e-3
+
+
+def test_flat_space_second_order():
+    """The dispersion error falls as (k h)^2 (second order, Sec. IV.A convergence claim)."""
+    e = []
+    for N in (16, 32):
+        om, ck = _plane_wave_omega(0.3, N, 0, steps=3000)
+        e.append(abs(om / ck - 1))
+    assert 3.0 < e[0] / e[1] < 5.0
+
+
+def test_cs2_is_a_free_parameter():
+    """The weights only need sum w xi xi = cs^2 delta (App. B); the recovered wave speed
+    is c for any admissible cs^2."""
+    for cs2 in (0.2, 1 / 3):
+        om, ck = _plane_wave_omega(0.4, 64, 0, cs2=cs2)
+        assert abs(om / ck - 1) < 3e-3
+
+
+# ---------------------------------------------------------------- conservation ------------
+
+def test_mass_conservation_torus():
+    """Collision conserves rho = sum f (sum_i f_i^eq = rho, Eq. PressureCurvedSystem);
+    periodic streaming and lossless bounce-back conserve sum_x rho exactly."""
+    spec = GridSpec(kind=KIND_TOROIDAL, n=(8, 12, 10), h=(1, 2 * math.pi / 12, 2 * math.pi / 10),
+                    x0=(4, 0, 0), c=0.4, geom=(20.0, 0, 0, 0),
+                    bc=(BC_BOUNCE, BC_BOUNCE, 0, 0, 0, 0))
+    g = oracle.OracleGrid(spec)
+    g.init([[20 + 8, 0, 0, 3.0, 1.0]])
+    m0 = g.get_f().sum()
+    g.step(50)
+    assert g.get_f().sum() == pytest.approx(m0, rel=1e-12, abs=1e-12)
+
+
+# ---------------------------------------------------------------- Bessel modes ------------
+
+def _annulus_spec(Nr=32, Nt=128, r_in=8.0, c=0.4, Nz=1, L=None):
+    kind = KIND_POLAR if Nz == 1 else KIND_CYLINDRICAL
+    bcz = (BC_PERIODIC, BC_PERIODIC) if Nz == 1 else (BC_ANTIBOUNCE, BC_ANTIBOUNCE)
+    return GridSpec(kind=kind, n=(Nr, Nt, Nz), h=(1, 2 * math.pi / Nt, 1), x0=(r_in, 0, 0),
+                    c=c, bc=(BC_BOUNCE, BC_ANTIBOUNCE, BC_PERIODIC, BC_PERIODIC) + bcz)
+
+
+def _mode_omega(spec, P0, probe, steps=3000):
+    g = oracle.OracleGrid(spec)
+    r = spec.x0[0] + np.arange(spec.n[0]) + 0.5
+    g.set_f(state_from_rho(r[None, :, None] * P0))
+    g.set_probes([probe], steps)
+    g.step(steps)
+    fr, am = oracle.spectrum(g.read_probes()[0], 3)
+    return fr[np.argmax(am)]
+
+
+@pytest.mark.parametrize("m,n", [(0, 0), (0, 1), (1, 0), (2, 0)])
+def test_annulus_bessel_modes(m, n):
+    """2-D annulus a < r < R, rigid inner wall (halfway bounce-back at r = a), Dirichlet outer
+    wall (anti-bounce-back at r = R): omega = c k with J_m(kR) Y_m'(ka) - Y_m(kR) J_m'(ka) = 0
+    (separation of variables, appendix "Radial modes of the pipe").  Within 0.2%."""
+    spec = _annulus_spec()
+    a, R = spec.x0[0], spec.x0[0] + spec.n[0]
+    k = annulus_wavenumbers(m, a, R, n + 1)[n]
+    r = a + np.arange(spec.n[0]) + 0.5
+    th = (np.arange(spec.n[1]) + 0.5) * spec.h[1]
+    P0 = (annulus_radial(m, k, a, r)[:, None] * np.cos(m * th)[None, :])[None]
+    om = _mode_omega(spec, P0, [spec.n[0] // 2, spec.n[1] // 16, 0])
+    assert abs(om / (spec.c * k) - 1) < 2e-3
+
+
+def test_cylinder_axial_mode():
+    """3-D cylinder with Dirichlet end caps: P = R_0(k r) sin(pi z / L),
+    omega = c sqrt(k^2 + (pi / L)^2) within 0.2%."""
+    Nz = 24
+    spec = _annulus_spec(Nr=24, Nt=64, r_in=6.0, Nz=Nz)
+    a, R = spec.x0[0], spec.x0[0] + spec.n[0]
+    k = annulus_wavenumbers(0, a, R, 1)[0]
+    r = a + np.arange(spec.n[0]) + 0.5
+    z = np.arange(Nz) + 0.5
+    P0 = np.sin(math.pi * z / Nz)[:, None, None] * annulus_radial(0, k, a, r)[None, :, None] \
+        * np.ones(spec.n[1])[None, None, :]
+    om = _mode_omega(spec, P0, [spec.n[0] // 3, 0, Nz // 3], steps=2500)
+    assert abs(om / (spec.c * math.hypot(k, math.pi / Nz)) - 1) < 2e-3
+
+
+def test_paper_pipe_zeros_golden():
+    """The printed zeros of (m+1) J_m(x) - x J_{m+1}(x), m = 0 (appendix table): the first
+    two are reproduced by the root finder the mode pins use; the third is a misprint."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "pipe_zeros_m0.txt"))
+            if l.strip() and not l.startswith("#")]
+    printed = [float(v) for _, v in rows]
+    ours = pipe_zeros(0, 3)
+    assert ours[0] == pytest.approx(printed[0], abs=3e-4)
+    assert ours[1] == pytest.approx(printed[1], abs=3e-4)
+    assert abs(ours[2] - printed[2]) > 1e-2 and ours[2] == pytest.approx(7.1558, abs=1e-4)
+
+
+# ---------------------------------------------------------------- finite differences ------
+
+def _embed_vec(kind, geom, r, w):
+    """The coordinate maps of Eqs. coordinatesTrumpet (exponential flare) and
+    CoordinatesTorus at theta = 0.3, vectorised (the test's own copy)."""
+    th = 0.3
+    if kind == KIND_TRUMPET:
+        a0, b, al = geom[:3]
+        s = (a0 + b * np.exp(al * w)) / (a0 + b)
+        return np.stack([r * s * np.cos(th), r * s * np.sin(th), w], -1)
+    R = geom[0]
+    return np.stack([(R + r * np.cos(w)) * np.cos(th), (R + r * np.cos(w)) * np.sin(th),
+                     r * np.sin(w)], -1)
+
+
+def _fd_geometry(kind, geom, r, w, eps=1e-5):
+    """sqrt g and g^{ab} on the (r, w) plane from a numerical Jacobian of the map."""
+    th = 0.3
+    def emb(rr, tt, ww):
+        if kind == KIND_TRUMPET:
+            a0, b, al = geom[:3]
+            s = (a0 + b * np.exp(al * ww)) / (a0 + b)
+            return np.stack([rr * s * np.cos(tt), rr * s * np.sin(tt), ww + 0 * rr], -1)
+        R = geom[0]
+        return np.stack([(R + rr * np.cos(ww)) * np.cos(tt), (R + rr * np.cos(ww)) * np.sin(tt),
+                         rr * np.sin(ww)], -1)
+    t = th + 0 * r
+    cols = [(emb(r + eps, t, w) - emb(r - eps, t, w)) / (2 * eps),
+            (emb(r, t + eps, w) - emb(r, t - eps, w)) / (2 * eps),
+            (emb(r, t, w + eps) - emb(r, t, w - eps)) / (2 * eps)]
+    J = np.stack(cols, -1)
+    g = np.einsum("...ka,...kb->...ab", J, J)
+    return np.sqrt(np.linalg.det(g)), np.linalg.inv(g)
+
+
+def _fd_solve(kind, geom, c, r0, L_r, n_ang, L_z, pulse, T, sub):
+    """Leapfrog FD solve of P_tt = c^2 (g^{ab} d_a d_b P - G^b d_b P) (Eq. waves expanded,
+    G^b = -(1/sqrt g) d_a (sqrt g g^{ab})) on the axisymmetric (r, w) plane, w = z
+    (trumpet) or phi (torus, periodic); second-order differences on a grid sub times finer
+    than the unit lattice.  Returns P at r = r0 + j / sub, w = l h_w."""
+    hr = 1.0 / sub
+    nr = int(round(L_r * sub)) + 1
+    if kind == KIND_TOROIDAL:
+        nw = n_ang * sub
+        hw = 2 * math.pi / nw
+    else:
+        hw = hr
+        nw = int(round(L_z * sub)) + 1
+    r1 = r0 + np.arange(nr) * hr
+    w1 = np.arange(nw) * hw
+    r, w = np.meshgrid(r1, w1, indexing="ij")
+    sg, gi = _fd_geometry(kind, geom, r, w)
+
+    def d_r(F):
+        out = np.zeros_like(F)
+        out[1:-1] = (F[2:] - F[:-2]) / (2 * hr)
+        out[0] = (F[1] - F[0]) / hr
+        out[-1] = (F[-1] - F[-2]) / hr
+        return out
+
+    def d_w(F):
+        if kind == KIND_TOROIDAL:
+            return (np.roll(F, -1, 1) - np.roll(F, 1, 1)) / (2 * hw)
+        out = np.zeros_like(F)
+        out[:, 1:-1] = (F[:, 2:] - F[:, :-2]) / (2 * hw)
+        out[:, 0] = (F[:, 1] - F[:, 0]) / hw
+        out[:, -1] = (F[:, -1] - F[:, -2]) / hw
+        return out
+
+    Gr = -(d_r(sg * gi[..., 0, 0]) + d_w(sg * gi[..., 0, 2])) / sg
+    Gw = -(d_r(sg * gi[..., 2, 0]) + d_w(sg * gi[..., 2, 2])) / sg
+    X = _embed_vec(kind, geom, r, w)
+    d2 = ((X - np.array(pulse[:3])) ** 2).sum(-1)
+    P = np.exp(-d2 / (2 * pulse[3] ** 2)) * pulse[4]
+
+    def rhs(P):
+        Prr = np.zeros_like(P)
+        Prr[1:-1] = (P[2:] - 2 * P[1:-1] + P[:-2]) / hr**2
+        if kind == KIND_TOROIDAL:
+            Pww = (np.roll(P, -1, 1) - 2 * P + np.roll(P, 1, 1)) / hw**2
+        else:
+            Pww = np.zeros_like(P)
+            Pww[:, 1:-1] = (P[:, 2:] - 2 * P[:, 1:-1] + P[:, :-2]) / hw**2
+        out = (gi[..., 0, 0] * Prr + 2 * gi[..., 0, 2] * d_r(d_w(P)) + gi[..., 2, 2] * Pww
+               - Gr * d_r(P) - Gw * d_w(P))
+        out[0] = out[-1] = 0.0
+        if kind != KIND_TOROIDAL:
+            out[:, 0] = out[:, -1] = 0.0
+        return c * c * out
+
+    hmin = min(hr, r0 * hw) if kind == KIND_TOROIDAL else hr
+    nsub = int(math.ceil(T / (0.3 * hmin / c)))
+    dt = T / nsub
+    Pm = P.copy()
+    Pc = P + 0.5 * dt * dt * rhs(P)
+    for _ in range(nsub - 1):
+        Pm, Pc = Pc, 2 * Pc - Pm + dt * dt * rhs(Pc)
+    return Pc
+
+
+@pytest.mark.parametrize("kind", [KIND_TRUMPET, KIND_TOROIDAL], ids=["trumpet", "torus"])
+def test_finite_difference_second_order(kind):
+    """The oracle agrees with a fine finite-difference solve of the paper's target equation
+    (Eq. waves) and the gap shrinks ~4x when the lattice is refined 2x (second order, the
+    initial layer of the f = f^eq start included)."""
+    c_phys, T_phys, L_r = 0.4, 10.0, 40.0
+    if kind == KIND_TRUMPET:
+        r0, sub = 8.0, 8
+        geom, L_z, n_ang = (20.0, 4.0, 0.05, 0.0), 40.0, 1
+        centre = _embed_vec(kind, geom, np.array(28.0), np.array(20.0))
+    else:  # minor angle resolved to ~0.4-1.4 physical units per cell
+        r0, sub = 16.0, 4
+        geom, L_z, n_ang = (100.0, 0.0, 0.0, 0.0), 0.0, 256
+        centre = _embed_vec(kind, geom, np.array(36.0), np.array(1.0))
+    pulse = tuple(centre) + (3.0, 1.0)
+    P_fd = _fd_solve(kind, geom, c_phys, r0, L_r, n_ang, L_z, pulse, T_phys, sub)
+    errs = []
+    for ref in (1, 2):
+        h = 1.0 / ref
+        Nr = int(L_r * ref)
+        if kind == KIND_TRUMPET:
+            Nw = int(L_z * ref)
+            spec = GridSpec(kind=kind, n=(Nr, 1, Nw), h=(h, 2 * math.pi, h), x0=(r0, 0.3 - math.pi, 0),
+                            c=c_phys * h, geom=geom, profile=PROFILE_EXP,
+                            bc=(BC_BOUNCE, BC_BOUNCE, 0, 0, BC_BOUNCE, BC_BOUNCE))
+            jw = ((np.arange(Nw) + 0.5) * h * sub).astype(int)
+        else:
+            Nw = n_ang * ref
+            spec = GridSpec(kind=kind, n=(Nr, 1, Nw), h=(h, 2 * math.pi, 2 * math.pi / Nw),
+                            x0=(r0, 0.3 - math.pi, 0), c=c_phys * h, geom=geom,
+                            bc=(BC_BOUNCE, BC_BOUNCE, 0, 0, 0, 0))
+            jw = ((np.arange(Nw) + 0.5) * (sub // ref)).astype(int)
+        g = oracle.OracleGrid(spec)
+        g.init([pulse])
+        g.step(int(round(T_phys / h)))
+        P = g.get_P()[:, :, 0]  # (N3, N1)
+        jr = ((np.arange(Nr) + 0.5) * h * sub).astype(int)
+        ref_P = P_fd[np.ix_(jr, jw)].T
+        errs.append(np.linalg.norm(P - ref_P) / np.linalg.norm(ref_P))
+    assert errs[0] < 0.1, errs
+    assert errs[0] / errs[1] > 3.0, errs
+
+
+# ---------------------------------------------------------------- step operator -----------
+
+def _step_matrix(spec):
+    g = oracle.OracleGrid(spec)
+    n = 7 * spec.nodes
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        g.set_f(e)
+        g.step(1)
+        A[:, j] = g.get_f().reshape(-1)
+    return A
+
+
+TINY = [
+    GridSpec(kind=KIND_POLAR, n=(6, 16, 1), h=(1, 2 * math.pi / 16, 1), x0=(2, 0, 0), c=0.4,
+             bc=(BC_BOUNCE, BC_ANTIBOUNCE, 0, 0, 0, 0)),
+    GridSpec(kind=KIND_CYLINDRICAL, n=(4, 8, 4), h=(1, 2 * math.pi / 8, 1), x0=(2, 0, 0),
+             c=0.4, bc=(BC_BOUNCE, BC_ANTIBOUNCE, 0, 0, BC_ANTIBOUNCE, BC_ANTIBOUNCE)),
+    GridSpec(kind=KIND_TRUMPET, n=(4, 8, 6), h=(1, 2 * math.pi / 8, 1), x0=(2, 0, 0), c=0.4,
+             geom=(6.0, 1.0, 0.2, 0), profile=PROFILE_EXP,
+             bc=(BC_BOUNCE, BC_BOUNCE, 0, 0, BC_BOUNCE, BC_BOUNCE)),
+    GridSpec(kind=KIND_TOROIDAL, n=(4, 8, 8), h=(1, 2 * math.pi / 8, 2 * math.pi / 8),
+             x0=(3, 0, 0), c=0.4, geom=(12.0, 0, 0, 0), bc=(BC_BOUNCE, BC_BOUNCE, 0, 0, 0, 0)),
+]
+
+
+@pytest.mark.parametrize("spec", TINY, ids=["polar", "cyl", "trumpet", "torus"])
+def test_step_operator_is_neutrally_stable(spec):
+    """tau = 1/2 makes the scheme non-dissipative (Eq. SecondOrder): with lossless walls the
+    linear step operator has spectral radius 1 at the lattice speeds the workloads use
+    (azimuthal lattice speed <= 1 at the innermost node, c = 0.4)."""
+    ev = np.linalg.eigvals(_step_matrix(spec))
+    assert np.abs(ev).max() < 1 + 1e-9
+
+
+def test_spectrum_finds_operator_eigenfrequencies():
+    """A run of the oracle, read by the spectrum estimator, shows peaks at arguments of
+    eigenvalues of the step operator (the discrete normal modes)."""
+    spec = TINY[0]
+    ev = np.linalg.eigvals(_step_matrix(spec))
+    angles = np.abs(np.angle(ev))
+    g = oracle.OracleGrid(spec)
+    rng = np.random.default_rng(7)
+    g.set_f(rng.standard_normal(7 * spec.nodes))
+    g.set_probes([[3, 5, 0]], 6000)
+    g.step(6000)
+    fr, am = oracle.spectrum(g.read_probes()[0], 4)
+    assert len(fr) >= 2
+    for f in fr:
+        assert np.min(np.abs(angles - f)) < 2e-5
+
+
+def test_spectrum_synthetic_sinusoids():
+    """Known frequencies and amplitudes are recovered from a sum of sinusoids."""
+    t = np.arange(5000)
+    om = np.array([0.0123, 0.0417, 0.1033])
+    amp = np.array([1.0, 0.5, 0.25])
+    x = sum(a * np.cos(w * t + p) for a, w, p in zip(amp, om, (0.1, 1.3, 2.0))) + 0.3
+    fr, am = oracle.spectrum(x, 3)
+    np.testing.assert_allclose(fr, om, rtol=2e-6)
+    np.testing.assert_allclose(am, amp, rtol=2e-2)
