@@ -418,12 +418,12 @@ def test_spectrum_finds_operator_eigenfrequencies():
     g = oracle.OracleGrid(spec)
     rng = np.random.default_rng(7)
     g.set_f(rng.standard_normal(7 * spec.nodes))
-    g.set_probes([[3, 5, 0]], 6000)
-    g.step(6000)
+    g.set_probes([[3, 5, 0]], 40000)
+    g.step(40000)
     fr, am = oracle.spectrum(g.read_probes()[0], 4)
     assert len(fr) >= 2
-    for f in fr:
-        assert np.min(np.abs(angles - f)) < 2e-5
+    for f in fr:  # leakage between the 7N modes bounds the agreement (~1e-6 at 40k steps)
+        assert np.min(np.abs(angles - f)) < 1e-5
 
 
 def test_spectrum_synthetic_sinusoids():
@@ -433,5 +433,5 @@ def test_spectrum_synthetic_sinusoids():
     amp = np.array([1.0, 0.5, 0.25])
     x = sum(a * np.cos(w * t + p) for a, w, p in zip(amp, om, (0.1, 1.3, 2.0))) + 0.3
     fr, am = oracle.spectrum(x, 3)
-    np.testing.assert_allclose(fr, om, rtol=2e-6)
+    np.testing.assert_allclose(fr, om, rtol=0, atol=1e-7)  # 1e-4 of a DFT bin
     np.testing.assert_allclose(am, amp, rtol=2e-2)
