@@ -1,0 +1,343 @@
+"""Benchmark of the fused curvilinear wave-LBM sweep on GB300.
+
+One benchmark step = one full run of the hot path on the 3-D cylinder workload
+(128 x 128 x 256 nodes, FP32 storage, 20 000 time steps of the fused stream + collide
+kernel with 16 probes recorded every step, then the device spectrum of the summed probes).
+Metric: MLUPS = nodes x time steps / seconds / 1e6 (whole job, all ranks).
+
+  value  device-timed: the initial state is rebuilt (untimed) before every step, then
+         CUDA events on the library's stream bracket lbw_step + lbw_spectrum.
+  e2e    the same run through the public C ABI from host buffers: lbw_init (host pulses),
+         lbw_probe (host probe nodes), lbw_step, lbw_probe_read (series to host) and
+         lbw_spectrum, all inside the timed region.
+The working set (two population buffers, 470 MB) is larger than the 129 MB L2, so no flush
+is needed between steps.  --impl reference times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbw_workloads as W  # noqa: E402
+
+LBM_STEPS = 20000
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            v = [x.strip() for x in l.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1]))
+                mx = max(mx, float(v[2]))
+            except ValueError:
+                continue
+            for n, flag in zip(names, v[5:9]):
+                if flag.lower() in ("active", "0x1", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    wl = W.workload("cylinder")
+    return wl
+
+
+def cpu_baseline(spec, pulses, probes, budget_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload: the full
+    lattice for as many time steps as fit in ~budget_s seconds of host time."""
+    import oracle
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    g = oracle.OracleGrid(spec)
+    g.init(pulses)
+    g.set_probes(probes, 1 << 16)
+    t0 = time.perf_counter()
+    g.step(1)
+    t1 = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(t1, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    g.step(n)
+    dt = time.perf_counter() - t0
+    mlups = spec.nodes * n / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"full {spec.n[0]}x{spec.n[1]}x{spec.n[2]} lattice, {n} time steps "
+                      f"({dt:.1f} s) of the FP64 C oracle, OpenMP over nodes"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    wl = workload()
+    spec = wl.spec
+    import oracle
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    g = oracle.OracleGrid(spec)
+    g.init(wl.pulses)
+    g.set_probes(wl.probes, 1 << 16)
+    g.step(1)
+    t0 = time.perf_counter()
+    g.step(1)
+    t1 = time.perf_counter() - t0
+    per_step = max(1, int(20.0 / max(t1, 1e-6)))  # ~20 s of host work per benchmark step
+    for _ in range(args.warmup):
+        g.step(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        g.step(per_step)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    mlups = spec.nodes * per_step * args.steps / total / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"cylinder {spec.n[0]}x{spec.n[1]}x{spec.n[2]}, "
+                               f"{per_step} time steps per benchmark step (bounded sample)",
+                   "nodes": spec.nodes},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} time steps of the full lattice per step"},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--lbm-steps", type=int, default=LBM_STEPS,
+                    help="time steps per benchmark step (default: the workload's 20000)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1705_01801_gb300 import lbw
+
+    wl = workload()
+    spec = wl.spec
+    lbm_steps = args.lbm_steps
+    stream = torch.cuda.Stream()
+    sh = lbw.ctypes.c_void_p(stream.cuda_stream)
+    grid = lbw.Grid(spec, stream=sh)
+    nprobe = wl.probes.shape[0]
+
+    def device_step(timed_events=None):
+        # initial state rebuilt outside the timed region; probes restarted
+        grid.init(wl.pulses)
+        grid.set_probes(wl.probes, lbm_steps)
+        stream.synchronize()
+        ev0, ev1, ev2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        ev0.record(stream)
+        grid.step(lbm_steps)
+        ev1.record(stream)
+        f, a = grid.spectrum(-1, 8)
+        ev2.record(stream)
+        ev2.synchronize()
+        return ev0.elapsed_time(ev2), ev0.elapsed_time(ev1), f
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed value
+    for _ in range(args.warmup):
+        device_step()
+    gpu_index = local
+    if os.environ.get("CUDA_VISIBLE_DEVICES"):
+        try:
+            gpu_index = int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local])
+        except ValueError:
+            pass
+    barrier()
+    tot_ms, step_ms, freqs = [], [], None
+    with ClockSampler(gpu_index) as clk:
+        for _ in range(args.steps):
+            t, s, freqs = device_step()
+            tot_ms.append(t)
+            step_ms.append(s)
+    barrier()
+    my_ms = sum(tot_ms)
+    if ws > 1:
+        tt = torch.tensor([my_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        my_ms = float(tt.item())
+    units = spec.nodes * lbm_steps * args.steps * ws
+    value = units / (my_ms / 1e3) / 1e6
+
+    # ---- roofline of the fused step kernel (algorithmic bytes: 7 loads + 7 stores)
+    bytes_per_node = 14 * 4
+    kernel_ms = sum(step_ms) / (args.steps * lbm_steps)
+    achieved = spec.nodes * bytes_per_node / (kernel_ms / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as fh:
+                tj = json.load(fh)
+            if tj.get("kernel_hash") == lbw_kernel_hash():
+                traffic = tj["bytes_per_launch_full_size"]
+        except Exception:
+            traffic = None
+
+    # ---- end to end through the C ABI with host buffers
+    host_pulses = np.ascontiguousarray(wl.pulses)
+    host_probes = np.ascontiguousarray(wl.probes.astype(np.int32))
+    L = lbw.lib()
+
+    def e2e_step():
+        lbw.lbw_init(grid.handle, host_pulses)
+        lbw.lbw_probe(grid.handle, host_probes, lbm_steps)
+        lbw.lbw_step(grid.handle, lbm_steps)
+        series = lbw.lbw_probe_read(grid.handle, nprobe, lbm_steps)
+        f, a = lbw.lbw_spectrum(grid.handle, -1, 8)
+        return series, f
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        series, _ = e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = units / e2e_s / 1e6
+    h2d = host_pulses.nbytes + host_probes.nbytes
+    d2h = nprobe * lbm_steps * 8 + 8 * 8 * 2
+
+    # kernel launches of this library inside the timed region: per step the fused kernels
+    # plus the spectrum (stats, window, log2 M Stockham passes, power, max, candidates,
+    # select, refine)
+    M = 1
+    while M < 4 * lbm_steps:
+        M *= 2
+    spectrum_launches = 2 + int(math.log2(M)) + 5
+    launches = args.steps * (lbm_steps + spectrum_launches)
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    base = None
+    if not args.no_cpu_baseline and ws == 1:
+        base = cpu_baseline(spec, wl.pulses, wl.probes)
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": my_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"cylinder (r, theta, z) {spec.n[0]}x{spec.n[1]}x{spec.n[2]}, "
+                               f"FP32 storage, {lbm_steps} time steps + spectrum per step, "
+                               f"{nprobe} probes, 8 random-phase Gaussian pulses",
+                   "nodes": spec.nodes, "time_steps_per_step": lbm_steps, "c": spec.c,
+                   "r_in": spec.x0[0],
+                   "l2": "working set 470 MB > 129 MB L2 (no flush needed)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "step_kernel<float>", "peak_source": peak_kind,
+                     "bytes_per_node": bytes_per_node, "kernel_us": kernel_ms * 1e3},
+        "cpu_baseline": base,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+        "spectrum_peaks": [round(float(x), 6) for x in freqs] if freqs is not None else None,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def lbw_kernel_hash():
+    import hashlib
+    p = os.path.join(ROOT, "paper_1705_01801_gb300", "csrc", "lbw_step.cu")
+    with open(p, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,158 @@
+/*
+ * lbw.h -- C ABI of the GB300 curvilinear wave lattice-Boltzmann library (liblbw.so).
+ *
+ * Method: Velasco, Munoz, Mendoza, "Lattice Boltzmann model for the simulation of the wave
+ * equation in curvilinear coordinates" (arXiv:1705.01801).  The library advances D3Q7
+ * populations on a Cartesian lattice of computational coordinates (q1, q2, q3) (Sec. III,
+ * first paragraph) with BGK relaxation at tau = 1/2 (Sec. II, Eq. eq:evolution and
+ * Eq. SecondOrder), the corrected equilibrium (Eq. EquilibriumCurvedSystemHermiteCorrected),
+ * the shifted momentum with the geometric forcing term (Eq. JCorrectionForce, Appendix A
+ * Eq. JShifted) and the lattice-weighted derivative (Eq. DerivativeFromTaylor, Appendix B).
+ *
+ * Conventions for every entry point:
+ *  - Plain C types only.  Pointers named host_* are host memory owned by the caller; the
+ *    library copies from / to them before returning.  Device memory of a grid is owned by
+ *    the library (allocated in lbw_create_grid on the grid's stream, freed in lbw_destroy).
+ *  - Every call returns an lbw_status and never aborts, traps or exits.  On failure the
+ *    thread-local message of lbw_last_error() says why.  LBW_ECUDA means a CUDA runtime call
+ *    failed (the message carries cudaGetErrorString).
+ *  - Work is enqueued on the CUDA stream given at creation (a cudaStream_t passed as void*,
+ *    0 = the legacy default stream).  Calls that return host data synchronise that stream.
+ *  - Node (q1, q2, q3) sits at physical coordinates x^a = x0[a] + (q_a + 1/2) h[a].
+ *    Memory layout of every per-node array: q2 fastest, then q1, then q3
+ *    (index = (q3 * n1 + q1) * n2 + q2); populations are seven such planes, i = 0..6 for
+ *    xi = 0, +e1, -e1, +e2, -e2, +e3, -e3.
+ *  - Frequencies are in radians per time step; time steps are 1 (Sec. II, delta_t = 1).
+ */
+#ifndef LBW_H
+#define LBW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBW_OK = 0,
+  LBW_EINVAL = 1,    /* invalid argument or descriptor */
+  LBW_ENOMEM = 2,    /* device or host allocation failed */
+  LBW_ECUDA = 3,     /* a CUDA runtime call failed */
+  LBW_EUNSTABLE = 4, /* a probe or field value is not finite */
+  LBW_ETIMEOUT = 5,  /* a bounded device wait ran out */
+  LBW_ESTATE = 6     /* call out of order (e.g. step before init) */
+} lbw_status;
+
+/* Coordinate systems of Sec. IV: Eq. cylindricalsystem (polar = cylindrical with n3 = 1),
+ * Eq. coordinatesTrumpet (flare s(z), see horn_profile) and Eq. CoordinatesTorus. */
+typedef enum {
+  LBW_CARTESIAN = 0,   /* (x, y, z) */
+  LBW_POLAR = 1,       /* (r, theta, z), n3 must be 1 */
+  LBW_CYLINDRICAL = 2, /* (r, theta, z) */
+  LBW_TRUMPET = 3,     /* (r, theta, z), x = r s(z) cos(theta), y = r s(z) sin(theta) */
+  LBW_TOROIDAL = 4     /* (r, theta major, phi minor), geom[0] = R */
+} lbw_metric;
+
+/* Face rules of Sec. IV.A (periodic, bounce-back with damping D, free = copy of the normal
+ * neighbour) and anti-bounce-back for a Dirichlet P = 0 wall. */
+typedef enum {
+  LBW_BC_PERIODIC = 0,
+  LBW_BC_BOUNCE = 1,
+  LBW_BC_ANTIBOUNCE = 2,
+  LBW_BC_FREE = 3
+} lbw_bc;
+
+/* Storage of the populations.  *S = 16-bit storage of f_i / w_i (the deviation from the
+ * rest state P = 0, scaled by the weight) with FP32 arithmetic. */
+typedef enum { LBW_F64 = 0, LBW_F32 = 1, LBW_F16S = 2, LBW_BF16S = 3 } lbw_prec;
+
+typedef struct {
+  int32_t kind;         /* lbw_metric */
+  int32_t n[3];         /* nodes along q1, q2, q3 (q2 is the fastest axis in memory) */
+  double h[3];          /* physical spacing per cell; angles: 2 pi / n */
+  double x0[3];         /* physical coordinate of the lower face of each axis (r_in for r) */
+  double c;             /* wave speed, physical units per time step */
+  double tau;           /* relaxation time; must be 0.5 (Sec. II) */
+  double cs2;           /* lattice cs^2, 0 < cs2 < 1/3; weights w0 = 1 - 3 cs2, wi = cs2 / 2 */
+  double damping;       /* D of the bounce-back rule, 0 < D <= 1 (1 = lossless) */
+  double geom[4];       /* torus: R; Bessel horn: Zmax, lambda; exp horn: a0, b, alpha */
+  int32_t horn_profile; /* 0 = Bessel horn s = (Zmax - z)^-lambda (Sec. IV.B),
+                           1 = exponential s = (a0 + b e^{alpha z}) / (a0 + b) */
+  int32_t bc[6];        /* lbw_bc of faces -q1, +q1, -q2, +q2, -q3, +q3 */
+  int32_t prec;         /* lbw_prec */
+  int32_t reserved;     /* must be 0 */
+} lbw_grid_desc;
+
+/* A Gaussian pulse P0 = amp exp(-|X - x|^2 / (2 sigma^2)) in the embedding distance. */
+typedef struct {
+  double x[3];
+  double sigma;
+  double amp;
+} lbw_pulse;
+
+typedef struct lbw_grid lbw_grid; /* opaque, library-owned */
+
+/* Validate desc, build the geometry of the lattice (sqrt g, g^{ab} and the contracted
+ * Christoffel symbols G^a = g^{bc} Gamma^a_{bc} of Sec. IV, written in lattice coordinates)
+ * and allocate two population buffers on `stream`.  Rejects with LBW_EINVAL: tau != 1/2,
+ * non-periodic angular axes, r <= 0 or a non-positive flare anywhere on the lattice or its
+ * ghost layer, and lattices whose largest c^2 (g^{11} + g^{22} + g^{33}) + 3 cs^2 exceeds
+ * 3.0 (the step operator's spectral radius exceeds 1 at 4 in flat space).  *out is set only
+ * on success; release it with lbw_destroy. */
+lbw_status lbw_create_grid(const lbw_grid_desc* desc, void* stream, lbw_grid** out);
+
+/* Initial state at rest (J' = 0 in the sense of Eq. JShifted): rho0 = sqrt(g) P0 with P0 the
+ * sum of the pulses, and post-collision populations f^eq(rho0, F(rho0) / 2).  n_pulses >= 0;
+ * host_pulses may be NULL when n_pulses is 0 (zero field).  Resets the step counter and
+ * the probe series. */
+lbw_status lbw_init(lbw_grid* g, const lbw_pulse* host_pulses, int32_t n_pulses);
+
+/* Advance n_steps >= 0 time steps (one fused stream + collide launch per step, captured in
+ * CUDA graphs).  Asynchronous on the grid's stream; registered probes record P after each
+ * step's streaming. */
+lbw_status lbw_step(lbw_grid* g, int64_t n_steps);
+
+/* Register n (0 <= n <= 64) probe nodes, host_q = n x (q1, q2, q3), with room for
+ * `capacity` samples each (further samples are dropped).  Resets the series. */
+lbw_status lbw_probe(lbw_grid* g, const int32_t* host_q, int32_t n, int64_t capacity);
+
+/* Copy the series to host_out (n x cap_per_probe doubles, probe-major); *n_steps receives
+ * the number of samples recorded (<= capacity).  LBW_EUNSTABLE if a sample is not finite. */
+lbw_status lbw_probe_read(lbw_grid* g, double* host_out, int64_t cap_per_probe,
+                          int64_t* n_steps);
+
+/* Mode frequencies of a recorded series (probe >= 0) or of the sum of all series
+ * (probe = -1), computed on the device: mean removed, Hann window, zero padding to the
+ * smallest power of two >= 4 T, |DFT|^2, the k strongest local maxima above 1e-3 of the
+ * largest (sorted by frequency), each refined by a parabola through log-power and 40
+ * golden-section steps on the windowed DTFT over +-1 bin.  host_freq / host_amp receive up
+ * to k values (rad/step, amplitude 2 |X| / sum w); *n_found how many. */
+lbw_status lbw_spectrum(lbw_grid* g, int32_t probe, int32_t k, double* host_freq,
+                        double* host_amp, int32_t* n_found);
+
+/* The same estimator on caller-provided series: host_x = n_series x T doubles. */
+lbw_status lbw_spectrum_series(const double* host_x, int64_t T, int32_t n_series, int32_t k,
+                               void* stream, double* host_freq, double* host_amp,
+                               int32_t* host_n_found);
+
+/* P = rho / sqrt(g) of the current state (rho = sum of the stored post-collision
+ * populations; the relaxation conserves it), N doubles in the layout above. */
+lbw_status lbw_get_field(lbw_grid* g, double* host_P);
+
+/* Checkpoint / resume: the seven population planes as doubles (7 x N, same layout). */
+lbw_status lbw_get_populations(lbw_grid* g, double* host_f);
+lbw_status lbw_set_populations(lbw_grid* g, const double* host_f);
+
+/* Number of time steps advanced since lbw_init. */
+lbw_status lbw_step_count(lbw_grid* g, int64_t* out);
+
+/* Frees the grid's device memory (stream-ordered) and graphs; NULL is allowed. */
+void lbw_destroy(lbw_grid* g);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* lbw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBW_H */

@@ -25,9 +25,11 @@ BC_PERIODIC, BC_BOUNCE, BC_ANTIBOUNCE, BC_FREE = range(4)
 PREC_F64, PREC_F32, PREC_F16S, PREC_BF16S = range(4)
 PROFILE_BESSEL, PROFILE_EXP = 0, 1
 
-# Largest stable lattice speed sqrt(c^2 g_q^{aa}) along any axis, measured on the oracle's
-# step operator (tests/test_oracle_pins.py::test_stability_bound); configs keep a margin.
-KAPPA_SAFE = 0.45
+# Azimuthal lattice speed c / (r h_theta) allowed at the innermost node.  The step operator
+# of every workload kind stays neutrally stable there at c = 0.4 (oracle eigenvalue pins);
+# the inner radius r_in follows from it.
+KAPPA_THETA = 1.0
+WAVE_SPEED = 0.4
 
 
 @dataclass(frozen=True)
@@ -52,12 +54,13 @@ class GridSpec:
         return replace(self, **kw)
 
 
-def r_inner(c: float, n_theta: int, kappa: float = KAPPA_SAFE) -> float:
-    """Inner radius at which the azimuthal lattice speed c / (r h_theta) equals kappa."""
-    return math.ceil(c / (kappa * (2.0 * math.pi / n_theta)))
+def r_inner(c: float, n_theta: int, kappa: float = KAPPA_THETA) -> float:
+    """Smallest whole inner radius whose first node (r_in + 1/2) has an azimuthal lattice
+    speed c / (r h_theta) <= kappa."""
+    return float(max(1, math.ceil(c / (kappa * (2.0 * math.pi / n_theta)) - 0.5)))
 
 
-def disk(n_r=128, n_theta=128, c=0.25, prec=PREC_F64) -> GridSpec:
+def disk(n_r=128, n_theta=128, c=WAVE_SPEED, prec=PREC_F64) -> GridSpec:
     r_in = r_inner(c, n_theta)
     return GridSpec(kind=KIND_POLAR, n=(n_r, n_theta, 1), h=(1.0, 2 * math.pi / n_theta, 1.0),
                     x0=(r_in, 0.0, 0.0), c=c,
@@ -65,7 +68,7 @@ def disk(n_r=128, n_theta=128, c=0.25, prec=PREC_F64) -> GridSpec:
                         BC_PERIODIC), prec=prec)
 
 
-def cylinder(n_r=128, n_theta=128, n_z=256, c=0.25, prec=PREC_F32) -> GridSpec:
+def cylinder(n_r=128, n_theta=128, n_z=256, c=WAVE_SPEED, prec=PREC_F32) -> GridSpec:
     r_in = r_inner(c, n_theta)
     return GridSpec(kind=KIND_CYLINDRICAL, n=(n_r, n_theta, n_z),
                     h=(1.0, 2 * math.pi / n_theta, 1.0), x0=(r_in, 0.0, 0.0), c=c,
@@ -85,7 +88,7 @@ def trumpet_params(seed: int, n_r: int, n_z: int):
     return a0, b, alpha
 
 
-def trumpet(n_r=256, n_theta=256, n_z=512, c=0.25, seed=3, prec=PREC_F32) -> GridSpec:
+def trumpet(n_r=256, n_theta=256, n_z=512, c=WAVE_SPEED, seed=3, prec=PREC_F32) -> GridSpec:
     r_in = r_inner(c, n_theta)
     a0, b, alpha = trumpet_params(seed, n_r, n_z)
     return GridSpec(kind=KIND_TRUMPET, n=(n_r, n_theta, n_z),
@@ -95,7 +98,7 @@ def trumpet(n_r=256, n_theta=256, n_z=512, c=0.25, seed=3, prec=PREC_F32) -> Gri
                     prec=prec)
 
 
-def torus(n_r=192, n_theta=1024, n_phi=256, c=0.25, prec=PREC_F32) -> GridSpec:
+def torus(n_r=192, n_theta=1024, n_phi=256, c=WAVE_SPEED, prec=PREC_F32) -> GridSpec:
     r_in = r_inner(c, n_phi)
     a = r_in + n_r
     R = 3.0 * a

@@ -1,0 +1,82 @@
+// lbw_internal.h -- types shared by the translation units of liblbw (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lbw.h"
+
+namespace lbw {
+
+// Per-(q1, q3) coefficients of the geometric forcing term, built on the host in FP64 from
+// the metric in lattice coordinates (Sec. IV) and rounded to the arithmetic type R.
+// With K^{ab} = c^2 g_q^{ab} - cs^2 delta^{ab} and rho the post-stream density, the
+// divergence of A^{ab} = rho K^{ab} by central differences (Eq. DerivativeFromTaylor) is
+//   D1 = A1p rho(q1+1) - A1m rho(q1-1) + C13p rho(q3+1) - C13m rho(q3-1) + S1 rho
+//   D2 = H22 (rho(q2+1) - rho(q2-1))
+//   D3 = B13p rho(q1+1) - B13m rho(q1-1) + C33p rho(q3+1) - C33m rho(q3-1) + S3 rho
+// where every coefficient already holds the factor 1/2, and a non-periodic face's ghost
+// (whose rho is a multiple of the node's own rho) is folded into S1 / S3 with the
+// neighbour coefficient set to zero.  mG1, mG3 = -c^2 G_q^1, -c^2 G_q^3.
+enum TableSlot {
+  T_A1P = 0, T_A1M, T_B13P, T_B13M, T_C13P, T_C13M, T_C33P, T_C33M,
+  T_S1, T_S3, T_H22, T_MG1, T_MG3, T_INVSG, T_SG, T_PAD, T_SLOTS
+};
+
+constexpr int kMaxProbes = 64;
+
+struct Grid {
+  lbw_grid_desc d;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;  // created here when the caller passed the legacy stream 0
+  int64_t nn = 0;          // nodes
+  size_t elem = 0;         // bytes per stored population value
+  void* f[2] = {nullptr, nullptr};  // ping-pong population buffers, 7 planes each
+  int cur = 0;             // which buffer holds the current post-collision state
+  void* table = nullptr;   // n3 * n1 * T_SLOTS values of R (float or double)
+  // probes
+  int32_t nprobe = 0;
+  int32_t* probe_q = nullptr;     // device, nprobe x 3
+  double* series = nullptr;       // device, nprobe x cap
+  int64_t cap = 0;
+  // device counters: [0] steps since init, [1] samples recorded, [2] last-block ticket
+  unsigned long long* counters = nullptr;
+  int64_t steps = 0;       // host mirror of counters[0]
+  bool initialised = false;
+  // launch shape of the step kernel
+  int bx = 0, by = 0, lz = 0;
+  dim3 grid_dim;
+  // captured step chains, one per parity of the starting buffer
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_len = 0;
+  // 16-bit storage scale: stored value = f_i * inv_w[i]
+  double w0 = 0, w1 = 0;
+};
+
+// error plumbing ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+lbw_status fail(lbw_status s, const std::string& msg);
+lbw_status cuda_fail(cudaError_t e, const char* what);
+
+#define LBW_CUDA(call)                                      \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return ::lbw::cuda_fail(e_, #call); \
+  } while (0)
+
+// kernels (lbw_step.cu) ---------------------------------------------------------------------
+cudaError_t launch_step(Grid* g, int src);             // one time step, buffer src -> 1-src
+cudaError_t launch_init(Grid* g, const double* d_pulses, int npulse);
+cudaError_t launch_field(Grid* g, double* d_P);        // P of the current state
+cudaError_t launch_to_double(Grid* g, double* d_f);    // current populations -> doubles
+cudaError_t launch_from_double(Grid* g, const double* d_f);
+void step_launch_shape(Grid* g);                       // choose bx, by, lz, grid_dim
+
+// spectrum (lbw_spectrum.cu) ----------------------------------------------------------------
+lbw_status spectrum_device(const double* d_x, int64_t T, int32_t n_series, int32_t stride_series,
+                           bool sum_all, int32_t k, cudaStream_t s, double* h_freq,
+                           double* h_amp, int32_t* h_n);
+
+}  // namespace lbw

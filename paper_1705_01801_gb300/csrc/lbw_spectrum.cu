@@ -1,0 +1,304 @@
+// lbw_spectrum.cu -- mode frequencies of probe series, on the device, in FP64.
+//
+// The paper reads normal modes off driven frequency sweeps (Sec. IV.A, Fig. Fig.Frequencies;
+// Sec. IV.C, Fig. FreqTorus).  For a pulse-excited run the same modes are the peaks of the
+// probe signal's spectrum, estimated here:
+//   1. mean removed, Hann window w_t = 1/2 - 1/2 cos(2 pi t / (T - 1));
+//   2. zero padding to M = smallest power of two >= 4 T; radix-2 Stockham FFT
+//      (log2 M passes through global memory, natural-order output);
+//   3. |X_j|^2, local maxima above 1e-3 of the largest bin; the k strongest are chosen with
+//      warp-shuffle arg-max reductions (ties: lower bin) and sorted by frequency;
+//   4. each peak is refined by a parabola through log-power at j-1, j, j+1 and 40
+//      golden-section steps on the windowed DTFT over +-1 bin (one CTA per peak; the DTFT
+//      sum uses per-thread chunks with a rotation recurrence for e^{-i omega t}).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lbw_internal.h"
+
+namespace lbw {
+namespace {
+
+constexpr int kThreads = 512;
+constexpr double kGolden = 0.6180339887498949;
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+// mean of the (summed) series and sum of the window weights
+__global__ void stats_kernel(const double* __restrict__ x, long long T, int nser, long long stride,
+                             double* out) {
+  __shared__ double red[32];
+  double s = 0.0, sw = 0.0;
+  for (long long t = threadIdx.x; t < T; t += blockDim.x) {
+    double v = 0.0;
+    for (int p = 0; p < nser; ++p) v += x[(long long)p * stride + t];
+    s += v;
+    sw += 0.5 - 0.5 * cospi(2.0 * (double)t / (double)(T - 1));
+  }
+  s = block_sum(s, red);
+  sw = block_sum(sw, red);
+  if (threadIdx.x == 0) {
+    out[0] = s / (double)T;
+    out[1] = sw;
+  }
+}
+
+// xw_t = w_t (x_t - mean) as complex, zero-padded to M
+__global__ void window_kernel(const double* __restrict__ x, long long T, int nser, long long stride,
+                              const double* __restrict__ stats, long long M, double2* a,
+                              double* xw) {
+  const double mean = stats[0];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < M;
+       t += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (t < T) {
+      for (int p = 0; p < nser; ++p) v += x[(long long)p * stride + t];
+      v = (0.5 - 0.5 * cospi(2.0 * (double)t / (double)(T - 1))) * (v - mean);
+      xw[t] = v;
+    }
+    a[t] = make_double2(v, 0.0);
+  }
+}
+
+// one radix-2 Stockham pass: sub-transforms of size ns are combined into size 2 ns
+__global__ void stockham_kernel(const double2* __restrict__ in, double2* __restrict__ out,
+                                long long M, long long ns) {
+  const long long half = M >> 1;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < half;
+       j += (long long)gridDim.x * blockDim.x) {
+    const long long k = j & (ns - 1);
+    const double2 a0 = in[j], b = in[j + half];
+    double s, c;
+    sincospi((double)k / (double)ns, &s, &c);  // w = e^{-i pi k / ns}
+    const double2 a1 = make_double2(b.x * c + b.y * s, b.y * c - b.x * s);
+    const long long d = (j / ns) * 2 * ns + k;
+    out[d] = make_double2(a0.x + a1.x, a0.y + a1.y);
+    out[d + ns] = make_double2(a0.x - a1.x, a0.y - a1.y);
+  }
+}
+
+__global__ void power_kernel(const double2* __restrict__ X, long long M, double* P) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j <= M / 2;
+       j += (long long)gridDim.x * blockDim.x)
+    P[j] = X[j].x * X[j].x + X[j].y * X[j].y;
+}
+
+__global__ void max_kernel(const double* __restrict__ P, long long M, double* out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (long long j = 1 + threadIdx.x; j <= M / 2; j += blockDim.x) m = fmax(m, P[j]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) out[2] = m;
+  }
+}
+
+__global__ void candidates_kernel(const double* __restrict__ P, long long M,
+                                  const double* __restrict__ stats, double thresh,
+                                  long long* cand, unsigned long long* count) {
+  const double lim = thresh * stats[2];
+  for (long long j = 1 + blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M / 2;
+       j += (long long)gridDim.x * blockDim.x) {
+    const double p = P[j];
+    if (p > P[j - 1] && p >= P[j + 1] && p >= lim) {
+      unsigned long long s = atomicAdd(count, 1ULL);
+      cand[s] = j;
+    }
+  }
+}
+
+// better(a, b): higher power wins, equal power -> lower bin
+__device__ __forceinline__ bool better(double pa, long long ja, double pb, long long jb) {
+  return pa > pb || (pa == pb && ja < jb);
+}
+
+// k rounds of a block-wide arg-max over the candidate list (warp shuffles), then sort
+__global__ void select_kernel(const double* __restrict__ P, long long* cand,
+                              const unsigned long long* __restrict__ count, int k,
+                              long long* chosen, int* n_chosen) {
+  __shared__ double sp[32];
+  __shared__ long long sj[32];
+  __shared__ long long pick[64];
+  const long long n = (long long)*count;
+  int got = 0;
+  for (int r = 0; r < k; ++r) {
+    double bp = -1.0;
+    long long bj = -1;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+      const long long j = cand[i];
+      if (j < 0) continue;
+      if (bj < 0 || better(P[j], j, bp, bj)) { bp = P[j]; bj = j; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double op = __shfl_down_sync(0xffffffffu, bp, o);
+      const long long oj = __shfl_down_sync(0xffffffffu, bj, o);
+      if (oj >= 0 && (bj < 0 || better(op, oj, bp, bj))) { bp = op; bj = oj; }
+    }
+    if ((threadIdx.x & 31) == 0) { sp[threadIdx.x >> 5] = bp; sj[threadIdx.x >> 5] = bj; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      bp = threadIdx.x < (blockDim.x >> 5) ? sp[threadIdx.x] : -1.0;
+      bj = threadIdx.x < (blockDim.x >> 5) ? sj[threadIdx.x] : -1;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double op = __shfl_down_sync(0xffffffffu, bp, o);
+        const long long oj = __shfl_down_sync(0xffffffffu, bj, o);
+        if (oj >= 0 && (bj < 0 || better(op, oj, bp, bj))) { bp = op; bj = oj; }
+      }
+      if (threadIdx.x == 0) sj[0] = bj;
+    }
+    __syncthreads();
+    const long long win = sj[0];
+    __syncthreads();
+    if (win < 0) break;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x)
+      if (cand[i] == win) cand[i] = -1;
+    if (threadIdx.x == 0) pick[got] = win;
+    ++got;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int a = 1; a < got; ++a) {  // insertion sort by frequency
+      long long v = pick[a];
+      int b = a - 1;
+      while (b >= 0 && pick[b] > v) { pick[b + 1] = pick[b]; --b; }
+      pick[b + 1] = v;
+    }
+    for (int a = 0; a < got; ++a) chosen[a] = pick[a];
+    *n_chosen = got;
+  }
+}
+
+// |sum_t xw_t e^{-i omega t}|^2 over the block
+__device__ double dtft_power(const double* __restrict__ xw, long long T, double omega, double* red) {
+  const long long chunk = (T + blockDim.x - 1) / blockDim.x;
+  const long long t0 = threadIdx.x * chunk, t1 = min(T, t0 + chunk);
+  double re = 0.0, im = 0.0;
+  if (t0 < t1) {
+    double s, c, ds, dc;
+    sincos(omega * (double)t0, &s, &c);
+    sincos(omega, &ds, &dc);
+    for (long long t = t0; t < t1; ++t) {
+      re += xw[t] * c;
+      im -= xw[t] * s;
+      const double cn = c * dc - s * ds;
+      s = s * dc + c * ds;
+      c = cn;
+    }
+  }
+  re = block_sum(re, red);
+  im = block_sum(im, red);
+  return re * re + im * im;
+}
+
+__global__ void refine_kernel(const double* __restrict__ xw, long long T, const double* __restrict__ P,
+                              long long M, const long long* __restrict__ chosen,
+                              const int* __restrict__ n_chosen, const double* __restrict__ stats,
+                              double* freq, double* amp) {
+  __shared__ double red[32];
+  const int p = blockIdx.x;
+  if (p >= *n_chosen) return;
+  const long long j = chosen[p];
+  const double la = log(P[j - 1]), lb = log(P[j]), lc = log(P[j + 1]);
+  const double den = la - 2.0 * lb + lc;
+  double delta = (den < 0.0) ? 0.5 * (la - lc) / den : 0.0;
+  if (!isfinite(delta)) delta = 0.0;
+  const double pi = 3.141592653589793238462643383279502884;
+  const double om = 2.0 * pi * ((double)j + delta) / (double)M;
+  const double halfw = 2.0 * pi / (double)M;
+  double a = om - halfw, b = om + halfw;
+  for (int it = 0; it < 40; ++it) {
+    const double c = b - kGolden * (b - a);
+    const double d = a + kGolden * (b - a);
+    const double fc = dtft_power(xw, T, c, red);
+    const double fd = dtft_power(xw, T, d, red);
+    if (fc > fd) b = d; else a = c;
+  }
+  const double w = 0.5 * (a + b);
+  const double pw = dtft_power(xw, T, w, red);
+  if (threadIdx.x == 0) {
+    freq[p] = w;
+    amp[p] = 2.0 * sqrt(pw) / stats[1];
+  }
+}
+
+}  // namespace
+
+lbw_status spectrum_device(const double* d_x, int64_t T, int32_t n_series, int32_t stride_series,
+                           bool sum_all, int32_t k, cudaStream_t s, double* h_freq,
+                           double* h_amp, int32_t* h_n) {
+  const int nser = sum_all ? n_series : 1;
+  long long M = 1;
+  while (M < 4 * T) M <<= 1;
+  // one scratch allocation: stats(4) | a(M) | b(M) | xw(T) | P(M/2+1) | cand(M/4+1) |
+  //                          count | chosen(64) | n_chosen | freq(64) | amp(64)
+  const size_t bytes = 4 * 8 + 2 * (size_t)M * 16 + (size_t)T * 8 + ((size_t)M / 2 + 1) * 8 +
+                       ((size_t)M / 4 + 1) * 8 + 8 + 64 * 8 + 8 + 64 * 8 + 64 * 8;
+  unsigned char* base = nullptr;
+  LBW_CUDA(cudaMallocAsync((void**)&base, bytes, s));
+  unsigned char* p = base;
+  auto take = [&](size_t n) { unsigned char* q = p; p += (n + 15) / 16 * 16; return q; };
+  double* stats = (double*)take(4 * 8);
+  double2* A = (double2*)take((size_t)M * 16);
+  double2* B = (double2*)take((size_t)M * 16);
+  double* xw = (double*)take((size_t)T * 8);
+  double* P = (double*)take(((size_t)M / 2 + 1) * 8);
+  long long* cand = (long long*)take(((size_t)M / 4 + 1) * 8);
+  unsigned long long* count = (unsigned long long*)take(8);
+  long long* chosen = (long long*)take(64 * 8);
+  int* n_chosen = (int*)take(8);
+  double* freq = (double*)take(64 * 8);
+  double* amp = (double*)take(64 * 8);
+  (void)p;
+
+  cudaError_t e = cudaMemsetAsync(count, 0, 8, s);
+  const int blocks = 152 * 4;
+  if (e == cudaSuccess) {
+    stats_kernel<<<1, 1024, 0, s>>>(d_x, T, nser, stride_series, stats);
+    window_kernel<<<blocks, 256, 0, s>>>(d_x, T, nser, stride_series, stats, M, A, xw);
+    double2 *in = A, *out = B;
+    for (long long ns = 1; ns < M; ns <<= 1) {
+      stockham_kernel<<<blocks, 256, 0, s>>>(in, out, M, ns);
+      std::swap(in, out);
+    }
+    power_kernel<<<blocks, 256, 0, s>>>(in, M, P);
+    max_kernel<<<1, 1024, 0, s>>>(P, M, stats);
+    candidates_kernel<<<blocks, 256, 0, s>>>(P, M, stats, 1e-3, cand, count);
+    select_kernel<<<1, 1024, 0, s>>>(P, cand, count, k, chosen, n_chosen);
+    refine_kernel<<<k, kThreads, 0, s>>>(xw, T, P, M, chosen, n_chosen, stats, freq, amp);
+    e = cudaGetLastError();
+  }
+  int nfound = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nfound, n_chosen, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && nfound > 0) {
+    e = cudaMemcpyAsync(h_freq, freq, sizeof(double) * nfound, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_amp, amp, sizeof(double) * nfound, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  cudaFreeAsync(base, s);
+  if (e != cudaSuccess) return cuda_fail(e, "spectrum");
+  *h_n = nfound;
+  return LBW_OK;
+}
+
+}  // namespace lbw

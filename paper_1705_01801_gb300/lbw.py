@@ -1,0 +1,261 @@
+"""Thin ctypes binding of liblbw.so (include/lbw.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of the
+library.  There is no CPU fallback; if the library cannot be built or loaded, ``lib()``
+raises.  PyTorch is used only to hand the library a CUDA stream (``torch_stream()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LBW_OK, LBW_EINVAL, LBW_ENOMEM, LBW_ECUDA, LBW_EUNSTABLE, LBW_ETIMEOUT, LBW_ESTATE = range(7)
+STATUS_NAMES = ["LBW_OK", "LBW_EINVAL", "LBW_ENOMEM", "LBW_ECUDA", "LBW_EUNSTABLE",
+                "LBW_ETIMEOUT", "LBW_ESTATE"]
+
+# every symbol the header declares (checked by tests/test_abi.py)
+EXPORTS = ["lbw_create_grid", "lbw_init", "lbw_step", "lbw_probe", "lbw_probe_read",
+           "lbw_spectrum", "lbw_spectrum_series", "lbw_get_field", "lbw_get_populations",
+           "lbw_set_populations", "lbw_step_count", "lbw_destroy", "lbw_last_error"]
+
+
+class lbw_grid_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("h", ctypes.c_double * 3),
+                ("x0", ctypes.c_double * 3), ("c", ctypes.c_double), ("tau", ctypes.c_double),
+                ("cs2", ctypes.c_double), ("damping", ctypes.c_double),
+                ("geom", ctypes.c_double * 4), ("horn_profile", ctypes.c_int32),
+                ("bc", ctypes.c_int32 * 6), ("prec", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class lbw_pulse(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_double * 3), ("sigma", ctypes.c_double), ("amp", ctypes.c_double)]
+
+
+class LbwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Build (if stale) and load the in-tree library; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(_build.build())
+            vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int32)
+            st = ctypes.c_int
+            sig = {
+                "lbw_create_grid": (st, [ctypes.POINTER(lbw_grid_desc), vp, ctypes.POINTER(vp)]),
+                "lbw_init": (st, [vp, ctypes.POINTER(lbw_pulse), i32]),
+                "lbw_step": (st, [vp, i64]),
+                "lbw_probe": (st, [vp, ip, i32, i64]),
+                "lbw_probe_read": (st, [vp, dp, i64, ctypes.POINTER(i64)]),
+                "lbw_spectrum": (st, [vp, i32, i32, dp, dp, ip]),
+                "lbw_spectrum_series": (st, [dp, i64, i32, i32, vp, dp, dp, ip]),
+                "lbw_get_field": (st, [vp, dp]),
+                "lbw_get_populations": (st, [vp, dp]),
+                "lbw_set_populations": (st, [vp, dp]),
+                "lbw_step_count": (st, [vp, ctypes.POINTER(i64)]),
+                "lbw_destroy": (None, [vp]),
+                "lbw_last_error": (ctypes.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def _check(status):
+    if status != LBW_OK:
+        raise LbwError(status, lib().lbw_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def torch_stream():
+    """Handle of torch's current CUDA stream (torch only provides the stream)."""
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def make_desc(spec) -> lbw_grid_desc:
+    """lbw_grid_desc from a ``lbw_workloads.GridSpec``."""
+    d = lbw_grid_desc()
+    d.kind = spec.kind
+    for a in range(3):
+        d.n[a] = int(spec.n[a])
+        d.h[a] = float(spec.h[a])
+        d.x0[a] = float(spec.x0[a])
+    d.c = spec.c
+    d.tau = 0.5
+    d.cs2 = spec.cs2
+    d.damping = spec.damping
+    for k in range(4):
+        d.geom[k] = float(spec.geom[k])
+    d.horn_profile = spec.profile
+    for k in range(6):
+        d.bc[k] = int(spec.bc[k])
+    d.prec = spec.prec
+    d.reserved = 0
+    return d
+
+
+def lbw_create_grid(desc: lbw_grid_desc, stream=None):
+    out = ctypes.c_void_p()
+    _check(lib().lbw_create_grid(ctypes.byref(desc), stream, ctypes.byref(out)))
+    return out
+
+
+def lbw_init(grid, pulses):
+    p = np.asarray(pulses, dtype=np.float64).reshape(-1, 5)
+    arr = (lbw_pulse * max(1, p.shape[0]))()
+    for k in range(p.shape[0]):
+        arr[k].x[0], arr[k].x[1], arr[k].x[2], arr[k].sigma, arr[k].amp = p[k]
+    _check(lib().lbw_init(grid, arr, p.shape[0]))
+
+
+def lbw_step(grid, n):
+    _check(lib().lbw_step(grid, int(n)))
+
+
+def lbw_probe(grid, q, capacity):
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.int32).reshape(-1, 3))
+    _check(lib().lbw_probe(grid, _ip(q), q.shape[0], int(capacity)))
+
+
+def lbw_probe_read(grid, n_probes, cap):
+    out = np.zeros((max(1, n_probes), max(1, cap)))
+    n = ctypes.c_int64()
+    _check(lib().lbw_probe_read(grid, _dp(out), max(1, cap), ctypes.byref(n)))
+    return out[:n_probes, : n.value]
+
+
+def lbw_spectrum(grid, probe, k):
+    f = np.zeros(k)
+    a = np.zeros(k)
+    n = ctypes.c_int32()
+    _check(lib().lbw_spectrum(grid, int(probe), int(k), _dp(f), _dp(a), ctypes.byref(n)))
+    return f[: n.value], a[: n.value]
+
+
+def lbw_spectrum_series(x, k, stream=None):
+    x = np.ascontiguousarray(np.atleast_2d(np.asarray(x, dtype=np.float64)))
+    ns, T = x.shape
+    f = np.zeros((ns, k))
+    a = np.zeros((ns, k))
+    n = np.zeros(ns, dtype=np.int32)
+    _check(lib().lbw_spectrum_series(_dp(x), T, ns, int(k), stream, _dp(f), _dp(a), _ip(n)))
+    return [(f[j, : n[j]], a[j, : n[j]]) for j in range(ns)]
+
+
+def lbw_get_field(grid, shape):
+    out = np.zeros(int(np.prod(shape)))
+    _check(lib().lbw_get_field(grid, _dp(out)))
+    return out.reshape(shape)
+
+
+def lbw_get_populations(grid, nn):
+    out = np.zeros(7 * nn)
+    _check(lib().lbw_get_populations(grid, _dp(out)))
+    return out
+
+
+def lbw_set_populations(grid, f):
+    a = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1))
+    _check(lib().lbw_set_populations(grid, _dp(a)))
+
+
+def lbw_step_count(grid):
+    n = ctypes.c_int64()
+    _check(lib().lbw_step_count(grid, ctypes.byref(n)))
+    return n.value
+
+
+def lbw_destroy(grid):
+    lib().lbw_destroy(grid)
+
+
+def lbw_last_error():
+    return lib().lbw_last_error().decode()
+
+
+class Grid:
+    """Convenience owner of one lbw_grid (a ``lbw_workloads.GridSpec`` in, numpy out)."""
+
+    def __init__(self, spec, stream=None):
+        self.spec = spec
+        self.n = tuple(int(v) for v in spec.n)
+        self.nn = int(np.prod(self.n))
+        self._h = lbw_create_grid(make_desc(spec), stream)
+        self._nprobe = 0
+        self._cap = 0
+
+    def close(self):
+        if self._h:
+            lbw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def init(self, pulses):
+        lbw_init(self._h, pulses)
+
+    def step(self, n):
+        lbw_step(self._h, n)
+
+    def set_probes(self, q, cap):
+        q = np.asarray(q, dtype=np.int32).reshape(-1, 3)
+        lbw_probe(self._h, q, cap)
+        self._nprobe, self._cap = q.shape[0], int(cap)
+
+    def read_probes(self):
+        return lbw_probe_read(self._h, self._nprobe, self._cap)
+
+    def spectrum(self, probe=0, k=8):
+        return lbw_spectrum(self._h, probe, k)
+
+    def get_P(self):
+        """P, shape (N3, N1, N2)."""
+        return lbw_get_field(self._h, (self.n[2], self.n[0], self.n[1]))
+
+    def get_f(self):
+        """Post-collision populations as doubles, shape (7, N3, N1, N2)."""
+        return lbw_get_populations(self._h, self.nn).reshape(7, self.n[2], self.n[0], self.n[1])
+
+    def set_f(self, f):
+        lbw_set_populations(self._h, f)
+
+    def step_count(self):
+        return lbw_step_count(self._h)
