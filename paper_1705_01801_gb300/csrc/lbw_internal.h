@@ -47,6 +47,8 @@ struct Grid {
   bool initialised = false;
   // launch shape of the step kernel
   int bx = 0, by = 0, lz = 0;
+  int tma_by = 0;          // 0: register-pipelined kernel; 4 or 7: TMA tile kernel rows
+  alignas(64) unsigned char tmaps[5 * 128];  // tensor maps: f[0] main/halo, f[1] main/halo, table
   dim3 grid_dim;
   // captured step chains, one per parity of the starting buffer
   cudaGraphExec_t graph[2] = {nullptr, nullptr};

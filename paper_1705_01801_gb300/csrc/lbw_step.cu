@@ -15,6 +15,7 @@
 // in a triple-buffered shared-memory plane, so each plane costs one __syncthreads.  All
 // loads and stores are coalesced along q2 (the fastest axis).  The q3 segments make the
 // grid a multiple of the resident CTA count on the 152 SMs.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -31,24 +32,28 @@ template <> struct Store<double> {
   using R = double;
   static constexpr bool kScaled = false;
   __device__ static R ld(const double* p) { return __ldg(p); }
+  __device__ static R ld_smem(const double* p) { return *p; }
   __device__ static void st(double* p, R v) { *p = v; }
 };
 template <> struct Store<float> {
   using R = float;
   static constexpr bool kScaled = false;
   __device__ static R ld(const float* p) { return __ldg(p); }
+  __device__ static R ld_smem(const float* p) { return *p; }
   __device__ static void st(float* p, R v) { *p = v; }
 };
 template <> struct Store<__half> {
   using R = float;
   static constexpr bool kScaled = true;
   __device__ static R ld(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ static R ld_smem(const __half* p) { return __half2float(*p); }
   __device__ static void st(__half* p, R v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
   using R = float;
   static constexpr bool kScaled = true;
   __device__ static R ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+  __device__ static R ld_smem(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   __device__ static void st(__nv_bfloat16* p, R v) { *p = __float2bfloat16_rn(v); }
 };
 
@@ -281,6 +286,498 @@ __global__ void __launch_bounds__(512) step_kernel(const StepArgs<S> a) {
   }
 }
 
+__device__ __forceinline__ int xi1_of(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
+
+// Two consecutive nodes along q2 per lane: 8-byte FP32 / 4-byte 16-bit / 16-byte FP64
+// vectors.
+template <typename S> struct Vec;
+template <> struct Vec<float> {
+  static constexpr int N = 2;  // nodes per lane
+  __device__ static void ld(const float* p, float o[2]) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+  __device__ static void st(float* p, const float o[2]) {
+    *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+  }
+};
+template <> struct Vec<double> {
+  static constexpr int N = 2;  // nodes per lane
+  __device__ static void ld(const double* p, double o[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+  __device__ static void st(double* p, const double o[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+  }
+};
+template <> struct Vec<__half> {
+  static constexpr int N = 2;  // nodes per lane
+  __device__ static void ld(const __half* p, float o[2]) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(p));
+    o[0] = a.x; o[1] = a.y;
+  }
+  __device__ static void st(__half* p, const float o[2]) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(o[0], o[1]);
+  }
+};
+template <> struct Vec<__nv_bfloat16> {
+  static constexpr int N = 2;  // nodes per lane
+  __device__ static void ld(const __nv_bfloat16* p, float o[2]) {
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    o[0] = a.x; o[1] = a.y;
+  }
+  __device__ static void st(__nv_bfloat16* p, const float o[2]) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(o[0], o[1]);
+  }
+};
+template <typename R> struct RVec;
+template <> struct RVec<float> {
+  __device__ static void ld(const float* p, float o[2]) { Vec<float>::ld(p, o); }
+  __device__ static void st(float* p, const float o[2]) { Vec<float>::st(p, o); }
+};
+template <> struct RVec<double> {
+  __device__ static void ld(const double* p, double o[2]) { Vec<double>::ld(p, o); }
+  __device__ static void st(double* p, const double o[2]) { Vec<double>::st(p, o); }
+};
+
+// ---------------------------------------------------------------- TMA tile kernel -------
+//
+// Raw post-collision planes are staged by the Tensor Memory Accelerator: per plane one elected
+// thread issues, for every population, a main box (BX columns x BY + 2 rows, rows shifted by
+// the population's xi1 so the pull of tile row w reads staged row w of every population) and
+// two V-column halo boxes at x0 - V and x0 + BX (periodic wraps resolved in the coordinates),
+// plus the tile's coefficient rows; all complete on the slot's mbarrier.  NB = 3 + D slots, D
+// planes ahead of the consumer.  CTA = (BY + 2) warps: warp w stands for lattice row
+// q1 = y0 - 1 + w (warps 0 and BY + 1 are halo rows; they also compute rho of the tile's two
+// halo columns), lane l owns nodes q2 = x0 + 2 l, x0 + 2 l + 1 (BX = 64).  Per plane u, step A
+// pulls the lane's populations (kept in registers) and writes rho into a double-buffered rho
+// plane; step B collides plane u - 1: one barrier per plane.  Face rules are reads of other
+// staged values (bounce-back / anti-bounce-back: the node's own opposite population; free:
+// the node's own population).  Nodes whose rule reaches outside the staged boxes (a halo row
+// on a face, a halo column on a q2 face, the first plane below the segment) pull from global
+// memory.  Every mbarrier wait is bounded: on expiry the CTA raises counters[3] and stops.
+
+constexpr int kTmaBX = 64;
+constexpr long long kWaitLimit = 1LL << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
+      ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(bar) : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n"
+      ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2),
+        "r"(bar) : "memory");
+}
+
+// Pull of one node from global memory with the face rules (rarely taken paths).
+template <typename S>
+__device__ __noinline__ void pull_global(const StepArgs<S>& a, int q1, int q2, int q3,
+                                         typename Store<S>::R* f) {
+  typename Store<S>::R g[7];
+  pull(a, q1, q2, q3, g);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) f[i] = g[i];
+}
+
+template <int BY>
+struct TmaLayout {
+  // per population: main box (BY+2) x BX, left / right halo boxes (BY+2) x V, 128-B aligned
+  template <typename S>
+  __host__ __device__ static constexpr int main_bytes() { return (BY + 2) * kTmaBX * (int)sizeof(S); }
+  __host__ __device__ static constexpr int halo_bytes() { return (((BY + 2) * 16) + 127) / 128 * 128; }
+  template <typename S>
+  __host__ __device__ static constexpr int pop_bytes() { return main_bytes<S>() + 2 * halo_bytes(); }
+  template <typename S>
+  __host__ __device__ static constexpr int slot_bytes() { return 7 * pop_bytes<S>(); }
+};
+
+template <typename S, int BY>
+__global__ void __launch_bounds__(32 * (BY + 2), 2) step_tma_kernel(
+    const StepArgs<S> a, const __grid_constant__ CUtensorMap tm_main,
+    const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_tab) {
+  using R = typename Store<S>::R;
+  constexpr int NPT = 2, BX = kTmaBX, D = 2, NB = 3 + D, ROWS = BY + 2;
+  constexpr int V = 16 / (int)sizeof(S);
+  constexpr int MB = TmaLayout<BY>::template main_bytes<S>();
+  constexpr int HB = TmaLayout<BY>::halo_bytes();
+  constexpr int POPB = TmaLayout<BY>::template pop_bytes<S>();
+  constexpr int SLOTB = TmaLayout<BY>::template slot_bytes<S>();
+  constexpr int PW = BX + 4;  // rho row: halo columns at 1 and BX + 2, nodes at 2 .. BX + 1
+  constexpr int PS = ROWS * PW;
+  constexpr int TABB = ((BY * T_SLOTS * (int)sizeof(R)) + 127) / 128 * 128;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int probe_list[kMaxProbes];
+  __shared__ int probe_cnt;
+  __shared__ int abort_flag;
+  __shared__ unsigned long long t_sample;
+
+  const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * a.lz;
+  const int z1 = min(z0 + a.lz, a.n3);
+  const bool p2 = a.bc[2] == LBW_BC_PERIODIC, p3 = a.bc[4] == LBW_BC_PERIODIC;
+
+  unsigned char* sbase = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<unsigned long long>(smem_raw) + 127) & ~127ULL);  // TMA wants 128 B
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(sbase);     // NB x 8 B
+  unsigned char* slots = sbase + 128;                                         // NB x SLOTB
+  R* rho_s = reinterpret_cast<R*>(slots + (size_t)NB * SLOTB);                // 2 x PS
+  R* tab_s = reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(rho_s) +
+                                  ((2 * PS * (int)sizeof(R) + 127) / 128) * 128);  // NB x TABB
+
+  auto slot_of = [&](int p) { return (p - (z0 - 1)) % NB; };
+  auto use_of = [&](int p) { return (p - (z0 - 1)) / NB; };
+  auto M = [&](int s, int i) { return reinterpret_cast<const S*>(slots + (size_t)s * SLOTB + i * POPB); };
+  auto L = [&](int s, int i) { return reinterpret_cast<const S*>(slots + (size_t)s * SLOTB + i * POPB + MB); };
+  auto Rh = [&](int s, int i) { return reinterpret_cast<const S*>(slots + (size_t)s * SLOTB + i * POPB + MB + HB); };
+
+  if (tid == 0) {
+    for (int k = 0; k < NB; ++k) mbar_init(smem_u32(&bars[k]));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    probe_cnt = 0;
+    abort_flag = 0;
+    t_sample = a.counters[1];
+  }
+  __syncthreads();
+  if (tid < a.nprobe) {
+    const int pq1 = a.probe_q[3 * tid], pq2 = a.probe_q[3 * tid + 1], pq3 = a.probe_q[3 * tid + 2];
+    if (pq1 >= y0 && pq1 < y0 + BY && pq2 >= x0 && pq2 < x0 + BX && pq3 >= z0 && pq3 < z1)
+      probe_list[atomicAdd(&probe_cnt, 1)] = tid;
+  }
+
+  // staging of raw plane p into its slot (one thread)
+  int last_issued = z0 - 2;
+  auto issue = [&](int p) {
+    last_issued = p;
+    const int s = slot_of(p);
+    const unsigned bar = smem_u32(&bars[s]);
+    const int pg = resolve(p, a.n3, p3);
+    if (p > z1 + 1 || pg < 0) {  // nothing to stage: complete the phase without data
+      mbar_expect_tx(bar, 0);
+      return;
+    }
+    int xl = x0 - V, xr = x0 + BX;
+    const bool hl = xl >= 0 || p2, hr = xr < a.n2 || p2;
+    if (xl < 0) xl += a.n2;
+    if (xr >= a.n2) xr -= a.n2;
+    const unsigned tx_pop = (unsigned)(ROWS * BX * sizeof(S)) + (hl ? ROWS * 16u : 0u) + (hr ? ROWS * 16u : 0u);
+    const bool tab = p >= z0 && p < z1;
+    mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * sizeof(R)) : 0u));
+    unsigned char* base = slots + (size_t)s * SLOTB;
+    for (int i = 0; i < 7; ++i) {
+      const int row = y0 - 1 - xi1_of(i);
+      tma_load_4d(smem_u32(base + i * POPB), &tm_main, x0, row, pg, i, bar);
+      if (hl) tma_load_4d(smem_u32(base + i * POPB + MB), &tm_halo, xl, row, pg, i, bar);
+      if (hr) tma_load_4d(smem_u32(base + i * POPB + MB + HB), &tm_halo, xr, row, pg, i, bar);
+    }
+    if (tab) tma_load_3d(smem_u32(reinterpret_cast<unsigned char*>(tab_s) + (size_t)s * TABB), &tm_tab, 0, y0, pg, bar);
+  };
+  auto wait_plane = [&](int p) {
+    const unsigned bar = smem_u32(&bars[slot_of(p)]);
+    const unsigned parity = (unsigned)(use_of(p) & 1);
+    long long it = 0;
+    while (!mbar_try_wait(bar, parity)) {
+      if (++it > kWaitLimit) {
+        abort_flag = 1;
+        a.counters[3] = 1;
+        break;
+      }
+    }
+  };
+
+  // this warp's row and this lane's nodes (fixed along q3)
+  const int q1 = y0 - 1 + w;
+  const int r1 = resolve(q1, a.n1, false);
+  const bool interior = w >= 1 && w <= BY;
+  const int c0 = lane * NPT;
+  const int q2 = x0 + c0;
+  const bool owner = interior && q1 < a.n1;
+  const bool q2lo = !p2 && q2 == 0, q2hi = !p2 && q2 + NPT - 1 == a.n2 - 1;
+
+  // pops 1 / 2 of a row: (population, staged row, factor); the pull or the q1-face rule
+  struct RowSrc { int pop1, row1, pop2, row2; R m1, m2; bool slow; };
+  auto row_src = [&](int rr1, int wr) {
+    RowSrc o{1, wr, 2, wr, R(1), R(1), false};
+    if (rr1 == 0) {
+      const int b = a.bc[0];
+      if (b == LBW_BC_FREE) { o.pop1 = 1; o.row1 = wr + 1; }
+      else { o.pop1 = 2; o.row1 = wr - 1; o.m1 = b == LBW_BC_BOUNCE ? a.damping : R(-1); }
+      if (wr == 0 || wr == ROWS - 1) o.slow = true;
+    }
+    if (rr1 == a.n1 - 1) {
+      const int b = a.bc[1];
+      if (b == LBW_BC_FREE) { o.pop2 = 2; o.row2 = wr - 1; }
+      else { o.pop2 = 1; o.row2 = wr + 1; o.m2 = b == LBW_BC_BOUNCE ? a.damping : R(-1); }
+      if (wr == 0 || wr == ROWS - 1) o.slow = true;
+    }
+    return o;
+  };
+  const RowSrc rs = row_src(r1, w);
+
+  // halo column node of a halo warp: warp 0 lane l -> (y0 + l, x0 - 1), warp BY+1 -> x0 + BX
+  const bool hcol = !interior && lane < BY;
+  const int hq1 = y0 + lane, hq2 = (w == 0) ? x0 - 1 : x0 + BX;
+  const int hr1 = resolve(hq1, a.n1, false), hr2 = resolve(hq2, a.n2, p2);
+  const RowSrc hs = row_src(hr1, lane + 1);
+  const bool hslow = hs.slow || (!p2 && hr2 >= 0 && (hr2 == 0 || hr2 == a.n2 - 1));
+  const int hrho = (lane + 1) * PW + ((w == 0) ? 1 : BX + 2);
+
+  // element of population i at staged (row, col), col in [-V, BX + V)
+  auto at = [&](int s, int i, int row, int col) -> R {
+    R v;
+    if (col < 0) v = Store<S>::ld_smem(L(s, i) + row * V + col + V);
+    else if (col >= BX) v = Store<S>::ld_smem(Rh(s, i) + row * V + col - BX);
+    else v = Store<S>::ld_smem(M(s, i) + row * BX + col);
+    return v;
+  };
+
+  // step A: populations of plane u into f, rho into rr and the rho plane
+  auto plane_A = [&](int u, R (&f)[7][NPT], R (&rr)[NPT]) {
+    const int r3 = resolve(u, a.n3, p3);
+    const int s0 = slot_of(u), sm = slot_of(u - 1), sp = slot_of(u + 1);
+    // pops 5 / 6: planes below / above, or the q3-face rule (slot, population, factor)
+    int s5 = sm, i5 = 5, s6 = sp, i6 = 6;
+    R m5 = R(1), m6 = R(1);
+    if (!p3 && r3 == 0) {
+      const int b = a.bc[4];
+      s5 = s0;
+      if (b != LBW_BC_FREE) { i5 = 6; m5 = b == LBW_BC_BOUNCE ? a.damping : R(-1); }
+    }
+    if (!p3 && r3 == a.n3 - 1) {
+      const int b = a.bc[5];
+      s6 = s0;
+      if (b != LBW_BC_FREE) { i6 = 5; m6 = b == LBW_BC_BOUNCE ? a.damping : R(-1); }
+    }
+    const R sc0 = Store<S>::kScaled ? a.w[0] : R(1), sc1 = Store<S>::kScaled ? a.w[1] : R(1);
+    if (r3 < 0 || r1 < 0) {
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) rr[k] = R(0);
+    } else if (rs.slow) {
+#pragma unroll 1
+      for (int k = 0; k < NPT; ++k) {
+        R g[7];
+        pull_global(a, r1, q2 + k, r3, g);
+#pragma unroll
+        for (int m = 0; m < NPT; ++m)
+          if (m == k) {
+#pragma unroll
+            for (int i = 0; i < 7; ++i) f[i][m] = g[i];
+            rr[m] = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+          }
+      }
+    } else {
+      R t3[NPT], t4[NPT];
+      Vec<S>::ld(M(s0, 0) + w * BX + c0, f[0]);
+      Vec<S>::ld(M(s0, rs.pop1) + rs.row1 * BX + c0, f[1]);
+      Vec<S>::ld(M(s0, rs.pop2) + rs.row2 * BX + c0, f[2]);
+      Vec<S>::ld(M(s0, 3) + w * BX + c0, t3);
+      Vec<S>::ld(M(s0, 4) + w * BX + c0, t4);
+      Vec<S>::ld(M(s5, i5) + w * BX + c0, f[5]);
+      Vec<S>::ld(M(s6, i6) + w * BX + c0, f[6]);
+      f[3][0] = lane == 0 ? Store<S>::ld_smem(L(s0, 3) + w * V + V - 1)
+                          : Store<S>::ld_smem(M(s0, 3) + w * BX + c0 - 1);
+      f[3][1] = t3[0];
+      f[4][0] = t4[1];
+      f[4][1] = lane == 31 ? Store<S>::ld_smem(Rh(s0, 4) + w * V)
+                           : Store<S>::ld_smem(M(s0, 4) + w * BX + c0 + 2);
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        f[0][k] *= sc0;
+        f[1][k] *= rs.m1 * sc1;
+        f[2][k] *= rs.m2 * sc1;
+        f[3][k] *= sc1;
+        f[4][k] *= sc1;
+        f[5][k] *= m5 * sc1;
+        f[6][k] *= m6 * sc1;
+      }
+      if (q2lo) {
+        const int b = a.bc[2];
+        f[3][0] = sc1 * (b == LBW_BC_FREE ? t3[0] : (b == LBW_BC_BOUNCE ? a.damping : R(-1)) * t4[0]);
+      }
+      if (q2hi) {
+        const int b = a.bc[3];
+        f[4][1] = sc1 * (b == LBW_BC_FREE ? t4[1] : (b == LBW_BC_BOUNCE ? a.damping : R(-1)) * t3[1]);
+      }
+#pragma unroll
+      for (int k = 0; k < NPT; ++k)
+        rr[k] = ((f[0][k] + f[1][k]) + (f[2][k] + f[3][k])) + ((f[4][k] + f[5][k]) + f[6][k]);
+    }
+    R* out = rho_s + (size_t)(u & 1) * PS;
+    RVec<R>::st(out + w * PW + 2 + c0, rr);
+    if (hcol) {
+      R h = R(0);
+      if (r3 >= 0 && hr1 >= 0 && hr2 >= 0) {
+        R g[7];
+        if (hslow) {
+          pull_global(a, hr1, hr2, r3, g);
+        } else {
+          const int hw = lane + 1, hc = hq2 - x0;  // staged row and column (-1 or BX)
+          g[0] = sc0 * at(s0, 0, hw, hc);
+          g[1] = hs.m1 * sc1 * at(s0, hs.pop1, hs.row1, hc);
+          g[2] = hs.m2 * sc1 * at(s0, hs.pop2, hs.row2, hc);
+          g[3] = sc1 * at(s0, 3, hw, hc - 1);
+          g[4] = sc1 * at(s0, 4, hw, hc + 1);
+          g[5] = m5 * sc1 * at(s5, i5, hw, hc);
+          g[6] = m6 * sc1 * at(s6, i6, hw, hc);
+        }
+        h = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+      }
+      out[hrho] = h;
+    }
+  };
+
+  // step B: collide plane z
+  auto plane_B = [&](int z, R (&fc)[7][NPT], const R (&rp)[NPT], const R (&rc)[NPT],
+                     const R (&rn)[NPT]) {
+    const R* cur = rho_s + (size_t)(z & 1) * PS + w * PW + 2 + c0;
+    R ru[NPT], rd[NPT], rl[NPT], rr[NPT];
+    RVec<R>::ld(cur + PW, ru);
+    RVec<R>::ld(cur - PW, rd);
+    rl[0] = cur[-1];
+    rl[1] = rc[0];
+    rr[0] = rc[1];
+    rr[1] = cur[2];
+    if (q2lo) rl[0] = a.s2lo * rc[0];
+    if (q2hi) rr[1] = a.s2hi * rc[1];
+    const R* T = tab_s + (size_t)slot_of(z) * (TABB / sizeof(R)) + (w - 1) * T_SLOTS;
+    R c[T_SLOTS];
+#pragma unroll
+    for (int k = 0; k < T_SLOTS; k += 4) {
+      if (sizeof(R) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(T + k);
+        c[k] = v.x; c[k + 1] = v.y; c[k + 2] = v.z; c[k + 3] = v.w;
+      } else {
+        const double2 v0 = *reinterpret_cast<const double2*>(T + k);
+        const double2 v1 = *reinterpret_cast<const double2*>(T + k + 2);
+        c[k] = v0.x; c[k + 1] = v0.y; c[k + 2] = v1.x; c[k + 3] = v1.y;
+      }
+    }
+    const R half = R(0.5);
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      const R rho = rc[k];
+      const R D1 = c[T_A1P] * ru[k] - c[T_A1M] * rd[k] + c[T_C13P] * rn[k] - c[T_C13M] * rp[k] + c[T_S1] * rho;
+      const R D3 = c[T_B13P] * ru[k] - c[T_B13M] * rd[k] + c[T_C33P] * rn[k] - c[T_C33M] * rp[k] + c[T_S3] * rho;
+      const R D2 = c[T_H22] * (rr[k] - rl[k]);
+      const R j1 = (fc[1][k] - fc[2][k]) + half * (c[T_MG1] * rho - D1);
+      const R j2 = (fc[3][k] - fc[4][k]) - half * D2;
+      const R j3 = (fc[5][k] - fc[6][k]) + half * (c[T_MG3] * rho - D3);
+      const R e = a.cs2 * rho;
+      fc[0][k] = a.two_w0 * rho - fc[0][k];
+      fc[1][k] = e + j1 - fc[1][k];
+      fc[2][k] = e - j1 - fc[2][k];
+      fc[3][k] = e + j2 - fc[3][k];
+      fc[4][k] = e - j2 - fc[4][k];
+      fc[5][k] = e + j3 - fc[5][k];
+      fc[6][k] = e - j3 - fc[6][k];
+    }
+    S* dst = a.fout + node(q1, q2, z, a.n1, a.n2);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      if (Store<S>::kScaled) {
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) fc[i][k] *= a.inv_w[i];
+      }
+      Vec<S>::st(dst + (long long)i * a.nn, fc[i]);
+    }
+    if (probe_cnt > 0 && t_sample < (unsigned long long)a.cap) {
+      for (int s2 = 0; s2 < probe_cnt; ++s2) {
+        const int k = probe_list[s2];
+        const int dq = a.probe_q[3 * k + 1] - q2;
+        if (a.probe_q[3 * k] == q1 && dq >= 0 && dq < NPT && a.probe_q[3 * k + 2] == z)
+          a.series[(long long)k * a.cap + t_sample] = (double)(dq == 0 ? rc[0] : rc[1]) * (double)c[T_INVSG];
+      }
+    }
+  };
+
+  // prologue: stage raw planes z0 - 1 .. z0 + 1 + D; rho of plane z0 - 1 (own column, whose
+  // pop 5 lies in the unstaged plane z0 - 2) from global memory; plane z0 from the slots
+  if (tid == 0)
+    for (int p = z0 - 1; p <= z0 + 1 + D; ++p) issue(p);
+  R fA[7][NPT], fB[7][NPT];
+  R rA[NPT], rB[NPT], rC[NPT];
+  {
+    const int u = z0 - 1, r3 = resolve(u, a.n3, p3);
+#pragma unroll 1
+    for (int k = 0; k < NPT; ++k) {
+      R v = R(0);
+      if (owner && r3 >= 0) {
+        R g[7];
+        pull_global(a, r1, q2 + k, r3, g);
+        v = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+      }
+      if (k == 0) rA[0] = v; else rA[1] = v;
+    }
+  }
+  wait_plane(z0 - 1);
+  wait_plane(z0);
+  wait_plane(z0 + 1);
+  plane_A(z0, fA, rB);
+
+  auto iter = [&](int z, R (&fc)[7][NPT], R (&fn)[7][NPT], R (&rp)[NPT], R (&rc)[NPT],
+                  R (&rn)[NPT]) {
+    wait_plane(z + 2);
+    __syncthreads();  // all reads of raw plane z - 1 and of the rho plane z + 1 (&1) are done
+    if (abort_flag) return false;
+    if (tid == 0) issue(z + 2 + D);
+    plane_A(z + 1, fn, rn);
+    if (owner) plane_B(z, fc, rp, rc, rn);
+    return true;
+  };
+  int z = z0;
+  bool ok = true;
+  for (; ok && z + 1 < z1; z += 2) {
+    ok = iter(z, fA, fB, rA, rB, rC);
+    if (ok) ok = iter(z + 1, fB, fA, rB, rC, rA);
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      const R t = rA[k];
+      rA[k] = rC[k];
+      rB[k] = t;
+    }
+  }
+  if (ok && z < z1) ok = iter(z, fA, fB, rA, rB, rC);
+
+  // drain: every staged plane has landed before the CTA exits (bounded)
+  __syncthreads();
+  if (tid == 0) {
+    for (int p = max(z0 - 1, last_issued - NB + 1); p <= last_issued; ++p) wait_plane(p);
+    __threadfence();
+    unsigned int ticket = atomicAdd(reinterpret_cast<unsigned int*>(&a.counters[2]), 1u);
+    if (ticket == a.nblocks - 1) {
+      a.counters[0] += 1;
+      if (a.nprobe > 0 && a.counters[1] < (unsigned long long)a.cap) a.counters[1] += 1;
+      a.counters[2] = 0;
+      __threadfence();
+    }
+  }
+}
+
 template <typename S>
 StepArgs<S> make_args(Grid* g, int src) {
   using R = typename Store<S>::R;
@@ -311,14 +808,110 @@ StepArgs<S> make_args(Grid* g, int src) {
   return a;
 }
 
+template <typename S, int BY>
+constexpr size_t tma_smem_bytes() {
+  using R = typename Store<S>::R;
+  constexpr int NB = 5, PS = (BY + 2) * (kTmaBX + 4);
+  constexpr int TABB = ((BY * T_SLOTS * (int)sizeof(R)) + 127) / 128 * 128;
+  return 128 /* alignment slack */ + 128 /* barriers */ +
+         (size_t)NB * TmaLayout<BY>::template slot_bytes<S>() +
+         ((2 * PS * sizeof(R) + 127) / 128) * 128 + (size_t)NB * TABB;
+}
+
 template <typename S>
 cudaError_t launch_step_t(Grid* g, int src) {
   using R = typename Store<S>::R;
   StepArgs<S> a = make_args<S>(g, src);
-  dim3 block(g->bx, g->by);
-  size_t smem = 3 * (size_t)(g->bx + 2) * (g->by + 2) * sizeof(R);
-  step_kernel<S><<<g->grid_dim, block, smem, g->stream>>>(a);
+  if (g->tma_by > 0) {
+    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(g->tmaps);
+    const dim3 block(32, g->tma_by + 2);
+    if (g->tma_by == 7)
+      step_tma_kernel<S, 7><<<g->grid_dim, block, tma_smem_bytes<S, 7>(), g->stream>>>(a, m[2 * src], m[2 * src + 1], m[4]);
+    else
+      step_tma_kernel<S, 4><<<g->grid_dim, block, tma_smem_bytes<S, 4>(), g->stream>>>(a, m[2 * src], m[2 * src + 1], m[4]);
+  } else {
+    dim3 block(g->bx, g->by);
+    size_t smem = 3 * (size_t)(g->bx + 2) * (g->by + 2) * sizeof(R);
+    step_kernel<S><<<g->grid_dim, block, smem, g->stream>>>(a);
+  }
   return cudaGetLastError();
+}
+
+template <typename S, int BY>
+int tma_regs_t() {
+  cudaFuncAttributes at;
+  if (cudaFuncGetAttributes(&at, step_tma_kernel<S, BY>) != cudaSuccess) {
+    cudaGetLastError();
+    return 255;
+  }
+  return at.numRegs;
+}
+
+template <typename S>
+cudaError_t tma_prepare_t(int by) {
+  return by == 7 ? cudaFuncSetAttribute(step_tma_kernel<S, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tma_smem_bytes<S, 7>())
+                 : cudaFuncSetAttribute(step_tma_kernel<S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tma_smem_bytes<S, 4>());
+}
+
+template <typename S>
+void tma_candidates(int* regs, size_t* smem) {
+  regs[0] = tma_regs_t<S, 4>();
+  regs[1] = tma_regs_t<S, 7>();
+  smem[0] = tma_smem_bytes<S, 4>();
+  smem[1] = tma_smem_bytes<S, 7>();
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+// Tensor maps of the two population buffers (4-D: q2, q1, q3, population) with the main
+// (64 x BY+2) and halo (V x BY+2) boxes, and of the coefficient table (3-D: slot, q1, q3).
+bool build_tmaps(Grid* g, int by) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  const int es = (int)g->elem, rs = g->d.prec == LBW_F64 ? 8 : 4;
+  CUtensorMapDataType dt = g->d.prec == LBW_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                           : g->d.prec == LBW_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                           : g->d.prec == LBW_F16S ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t dims[4] = {(cuuint64_t)g->d.n[1], (cuuint64_t)g->d.n[0], (cuuint64_t)g->d.n[2], 7};
+  const cuuint64_t strides[3] = {(cuuint64_t)g->d.n[1] * es, (cuuint64_t)g->d.n[1] * g->d.n[0] * es,
+                                 (cuuint64_t)g->nn * es};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint32_t box_main[4] = {(cuuint32_t)kTmaBX, (cuuint32_t)(by + 2), 1, 1};
+  const cuuint32_t box_halo[4] = {(cuuint32_t)(16 / es), (cuuint32_t)(by + 2), 1, 1};
+  CUtensorMap* m = reinterpret_cast<CUtensorMap*>(g->tmaps);
+  for (int b = 0; b < 2; ++b) {
+    if (encode(&m[2 * b], dt, 4, g->f[b], dims, strides, box_main, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    if (encode(&m[2 * b + 1], dt, 4, g->f[b], dims, strides, box_halo, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  const cuuint64_t tdims[3] = {(cuuint64_t)T_SLOTS, (cuuint64_t)g->d.n[0], (cuuint64_t)g->d.n[2]};
+  const cuuint64_t tstr[2] = {(cuuint64_t)T_SLOTS * rs, (cuuint64_t)T_SLOTS * rs * g->d.n[0]};
+  const cuuint32_t tbox[3] = {(cuuint32_t)T_SLOTS, (cuuint32_t)by, 1};
+  const cuuint32_t testr[3] = {1, 1, 1};
+  return encode(&m[4], rs == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                g->table, tdims, tstr, tbox, testr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // ---------------------------------------------------------------- initial state ----------
@@ -528,24 +1121,70 @@ cudaError_t launch_from_double(Grid* g, const double* d_f) {
                   [&](auto tag) { return launch_readout_t<decltype(tag)>(g, 2, nullptr, d_f); });
 }
 
-// CTA tile: BX columns along q2 (a multiple of 32, at most 128) by BY rows along q1 with
-// BX * BY = 512; q3 segments so the grid fills every resident CTA slot on the device.
+// Launch shape.  TMA tile kernel (q2 extent a multiple of 64, non-periodic q1): tile
+// 64 x BY with BY in {4, 7}; the resident CTAs per SM follow from shared memory and the
+// kernel's register count; the number of q3 segments minimises
+// waves x CTAs per SM x (planes per segment + 3) x (BY + 2), the bytes an SM moves with whole
+// waves counted.  Otherwise the register-pipelined kernel with 512-thread tiles.
 void step_launch_shape(Grid* g) {
   const int n1 = g->d.n[0], n2 = g->d.n[1], n3 = g->d.n[2];
+  int dev = 0, sms = 152, smem_max = 227 * 1024;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  g->tma_by = 0;
+  if (n2 % kTmaBX == 0 && g->d.bc[0] != LBW_BC_PERIODIC && g->nn * 7 < (1LL << 31)) {
+    int regs[2];
+    size_t smem[2];
+    switch (g->d.prec) {
+      case LBW_F64: tma_candidates<double>(regs, smem); break;
+      case LBW_F32: tma_candidates<float>(regs, smem); break;
+      case LBW_F16S: tma_candidates<__half>(regs, smem); break;
+      default: tma_candidates<__nv_bfloat16>(regs, smem);
+    }
+    const int bys[2] = {4, 7};
+    double best = 1e300;
+    for (int c = 0; c < 2; ++c) {
+      const int by = bys[c], threads = 32 * (by + 2);
+      if ((long long)smem[c] > smem_max || regs[c] > 255) continue;
+      const int rr = (regs[c] + 7) & ~7;
+      int per_sm = std::min<int>(2048 / threads, (int)((228LL * 1024) / (smem[c] + 1024)));
+      per_sm = std::max(1, std::min(per_sm, 65536 / (rr * threads)));
+      const long long tiles = (long long)(n2 / kTmaBX) * ((n1 + by - 1) / by);
+      const long long slots = (long long)sms * per_sm;
+      for (long long segs = 1; segs <= n3; ++segs) {
+        const int lz = (int)((n3 + segs - 1) / segs);
+        const long long blocks = tiles * ((n3 + lz - 1) / lz);
+        const long long waves = (blocks + slots - 1) / slots;
+        const double cost = (double)waves * per_sm * (lz + 3) * (by + 2);
+        if (cost < best) {
+          best = cost;
+          g->tma_by = by;
+          g->lz = lz;
+        }
+      }
+    }
+    if (g->tma_by > 0) {
+      cudaError_t e = dispatch(g->d.prec, [&](auto tag) { return tma_prepare_t<decltype(tag)>(g->tma_by); });
+      if (e == cudaSuccess && build_tmaps(g, g->tma_by)) {
+        g->grid_dim = dim3(n2 / kTmaBX, (n1 + g->tma_by - 1) / g->tma_by, (n3 + g->lz - 1) / g->lz);
+        return;
+      }
+      cudaGetLastError();
+      g->tma_by = 0;
+    }
+  }
   int bx = std::min(128, ((n2 + 31) / 32) * 32);
   int by = 512 / bx;
   g->bx = bx;
   g->by = by;
   const long long cols = (long long)((n2 + bx - 1) / bx) * ((n1 + by - 1) / by);
-  int dev = 0, sms = 152, per_sm = 2;
-  if (cudaGetDevice(&dev) == cudaSuccess)
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long slots = (long long)sms * per_sm;
-  long long segs = std::max<long long>(1, (slots + cols - 1) / cols);
+  const long long slots = (long long)sms * 2;
+  long long segs = std::max<long long>(1, slots / cols);
   segs = std::min<long long>(segs, n3);
-  int lz = (int)((n3 + segs - 1) / segs);
-  g->lz = lz;
-  g->grid_dim = dim3((n2 + bx - 1) / bx, (n1 + by - 1) / by, (n3 + lz - 1) / lz);
+  g->lz = (int)((n3 + segs - 1) / segs);
+  g->grid_dim = dim3((n2 + bx - 1) / bx, (n1 + by - 1) / by, (n3 + g->lz - 1) / g->lz);
 }
 
 }  // namespace lbw

@@ -25,14 +25,15 @@ pytestmark = pytest.mark.gpu
 
 TWO_PI = 2 * math.pi
 
-# shapes span several CTA tiles along q2 (128 wide) and q1 (4 rows) with ragged tails
+# shapes span several CTA tiles along q2 and q1 with ragged tails; q2 extents that are
+# multiples of 64 run the TMA tile kernel, the others the register-pipelined kernel
 SPECS = {
     "cartesian_mixed": GridSpec(kind=KIND_CARTESIAN, n=(9, 40, 11), h=(1, 1, 1), x0=(0, 0, 0),
                                 c=0.45, bc=(BC_FREE, BC_BOUNCE, BC_ANTIBOUNCE, BC_FREE,
                                             BC_PERIODIC, BC_PERIODIC), damping=0.9),
     "polar": GridSpec(kind=KIND_POLAR, n=(40, 64, 1), h=(1, TWO_PI / 64, 1), x0=(7, 0, 0),
                       c=0.4, bc=(BC_BOUNCE, BC_ANTIBOUNCE, 0, 0, 0, 0)),
-    "cylinder": GridSpec(kind=KIND_CYLINDRICAL, n=(21, 200, 19), h=(1, TWO_PI / 200, 1),
+    "cylinder": GridSpec(kind=KIND_CYLINDRICAL, n=(23, 192, 19), h=(1, TWO_PI / 192, 1),
                          x0=(13, 0, 0), c=0.4,
                          bc=(BC_BOUNCE, BC_ANTIBOUNCE, 0, 0, BC_ANTIBOUNCE, BC_FREE)),
     "trumpet_exp": GridSpec(kind=KIND_TRUMPET, n=(17, 96, 33), h=(1, TWO_PI / 96, 1),
@@ -43,7 +44,11 @@ SPECS = {
                                x0=(14, 0, 0), c=0.4, geom=(60.0, 0.2, 0, 0),
                                profile=PROFILE_BESSEL,
                                bc=(BC_BOUNCE, BC_BOUNCE, 0, 0, BC_BOUNCE, BC_FREE)),
-    "torus": GridSpec(kind=KIND_TOROIDAL, n=(13, 160, 24), h=(1, TWO_PI / 160, TWO_PI / 24),
+    # q2 extent of 50 is not a whole number of 16-byte vectors: register-pipelined kernel
+    "cylinder_unstaged": GridSpec(kind=KIND_CYLINDRICAL, n=(11, 50, 9), h=(1, TWO_PI / 50, 1),
+                                  x0=(9, 0, 0), c=0.4,
+                                  bc=(BC_BOUNCE, BC_FREE, 0, 0, BC_BOUNCE, BC_ANTIBOUNCE)),
+    "torus": GridSpec(kind=KIND_TOROIDAL, n=(13, 128, 24), h=(1, TWO_PI / 128, TWO_PI / 24),
                       x0=(4, 0, 0), c=0.4, geom=(40.0, 0, 0, 0),
                       bc=(BC_FREE, BC_BOUNCE, 0, 0, 0, 0)),
 }
