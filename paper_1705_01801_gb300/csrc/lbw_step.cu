@@ -292,7 +292,6 @@ __device__ __forceinline__ int xi1_of(int i) { return i == 1 ? 1 : (i == 2 ? -1 
 // vectors.
 template <typename S> struct Vec;
 template <> struct Vec<float> {
-  static constexpr int N = 2;  // nodes per lane
   __device__ static void ld(const float* p, float o[2]) {
     const float2 v = *reinterpret_cast<const float2*>(p);
     o[0] = v.x; o[1] = v.y;
@@ -302,7 +301,6 @@ template <> struct Vec<float> {
   }
 };
 template <> struct Vec<double> {
-  static constexpr int N = 2;  // nodes per lane
   __device__ static void ld(const double* p, double o[2]) {
     const double2 v = *reinterpret_cast<const double2*>(p);
     o[0] = v.x; o[1] = v.y;
@@ -312,7 +310,6 @@ template <> struct Vec<double> {
   }
 };
 template <> struct Vec<__half> {
-  static constexpr int N = 2;  // nodes per lane
   __device__ static void ld(const __half* p, float o[2]) {
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(p));
     o[0] = a.x; o[1] = a.y;
@@ -322,7 +319,6 @@ template <> struct Vec<__half> {
   }
 };
 template <> struct Vec<__nv_bfloat16> {
-  static constexpr int N = 2;  // nodes per lane
   __device__ static void ld(const __nv_bfloat16* p, float o[2]) {
     const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
     o[0] = a.x; o[1] = a.y;
@@ -351,7 +347,7 @@ template <> struct RVec<double> {
 // planes ahead of the consumer.  CTA = (BY + 2) warps: warp w stands for lattice row
 // q1 = y0 - 1 + w (warps 0 and BY + 1 are halo rows; they also compute rho of the tile's two
 // halo columns), lane l owns nodes q2 = x0 + 2 l, x0 + 2 l + 1 (BX = 64).  Per plane u, step A
-// pulls the lane's populations (kept in registers) and writes rho into a double-buffered rho
+// pulls the lane's populations (kept in registers) and writes rho into one of three rotating rho
 // plane; step B collides plane u - 1: one barrier per plane.  Face rules are reads of other
 // staged values (bounce-back / anti-bounce-back: the node's own opposite population; free:
 // the node's own population).  Nodes whose rule reaches outside the staged boxes (a halo row
@@ -359,21 +355,19 @@ template <> struct RVec<double> {
 // memory.  Every mbarrier wait is bounded: on expiry the CTA raises counters[3] and stops.
 
 constexpr int kTmaBX = 64;
-constexpr long long kWaitLimit = 1LL << 22;
+constexpr long long kWaitLimit = 1LL << 20;  // x up to 2 us per try: about 2 s
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
   unsigned done;
+  // the thread may sleep up to 2 us inside try_wait until the phase completes
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 2000;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(done) : "r"(bar), "r"(parity) : "memory");
   return done != 0;
@@ -417,20 +411,52 @@ struct TmaLayout {
   __host__ __device__ static constexpr int slot_bytes() { return 7 * pop_bytes<S>(); }
 };
 
+__device__ __forceinline__ void mbar_init_count(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(threads) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ T lds(const unsigned char* base, int byte_off) {
+  return *reinterpret_cast<const T*>(base + byte_off);
+}
+
+// Fused step, TMA-staged.  CTA = BY + 2 consumer warps + 1 producer warp.  Consumer warp w
+// stands for lattice row q1 = y0 - 1 + w (warps 0 and BY + 1 are halo rows; they also compute
+// rho of the tile's two halo columns), lane l owns nodes q2 = x0 + 2 l, x0 + 2 l + 1
+// (BX = 64).  The producer's lane 0 stages raw plane p into slot (p - z0 + 1) mod NB: per
+// population a main box of BX columns x BY + 2 rows (rows shifted by the population's xi1, so
+// the pull of tile row w reads staged row w of every population) and two V-column halo
+// boxes at x0 - V and x0 + BX (periodic wraps in the coordinates), plus the tile's
+// coefficient rows; the slot's full mbarrier completes on the bytes, and a slot is refilled
+// only after every consumer warp has released it (empty mbarrier), so the producer runs up to
+// NB - 3 planes ahead.  Per plane u the consumers pull their populations (kept in registers)
+// and write rho into one of three rotating rho planes (step A), synchronise among themselves
+// (named barrier) and collide plane u - 1 (step B).  Face rules are reads of other staged
+// values (bounce-back / anti-bounce-back: the node's own opposite population; free: the
+// node's own population); nodes whose rule leaves the staged boxes (a halo row on a face, a
+// halo column on a q2 face, the plane below the segment) pull from global memory.  Every
+// mbarrier wait is bounded: on expiry counters[3] is raised and the CTA stops.
 template <typename S, int BY>
-__global__ void __launch_bounds__(32 * (BY + 2), 2) step_tma_kernel(
+__global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     const StepArgs<S> a, const __grid_constant__ CUtensorMap tm_main,
     const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_tab) {
   using R = typename Store<S>::R;
-  constexpr int NPT = 2, BX = kTmaBX, D = 2, NB = 3 + D, ROWS = BY + 2;
-  constexpr int V = 16 / (int)sizeof(S);
+  constexpr int NPT = 2, BX = kTmaBX, NB = 5, ROWS = BY + 2, NCW = ROWS;  // consumer warps
+  constexpr int ES = (int)sizeof(S), RS = (int)sizeof(R);
+  constexpr int V = 16 / ES;
   constexpr int MB = TmaLayout<BY>::template main_bytes<S>();
   constexpr int HB = TmaLayout<BY>::halo_bytes();
   constexpr int POPB = TmaLayout<BY>::template pop_bytes<S>();
   constexpr int SLOTB = TmaLayout<BY>::template slot_bytes<S>();
   constexpr int PW = BX + 4;  // rho row: halo columns at 1 and BX + 2, nodes at 2 .. BX + 1
   constexpr int PS = ROWS * PW;
-  constexpr int TABB = ((BY * T_SLOTS * (int)sizeof(R)) + 127) / 128 * 128;
+  constexpr int TABB = ((BY * T_SLOTS * RS) + 127) / 128 * 128;
+  constexpr int RHOB = ((3 * PS * RS) + 127) / 128 * 128;  // three rho planes
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int probe_list[kMaxProbes];
   __shared__ int probe_cnt;
@@ -442,22 +468,20 @@ __global__ void __launch_bounds__(32 * (BY + 2), 2) step_tma_kernel(
   const int z1 = min(z0 + a.lz, a.n3);
   const bool p2 = a.bc[2] == LBW_BC_PERIODIC, p3 = a.bc[4] == LBW_BC_PERIODIC;
 
-  unsigned char* sbase = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<unsigned long long>(smem_raw) + 127) & ~127ULL);  // TMA wants 128 B
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(sbase);     // NB x 8 B
-  unsigned char* slots = sbase + 128;                                         // NB x SLOTB
-  R* rho_s = reinterpret_cast<R*>(slots + (size_t)NB * SLOTB);                // 2 x PS
-  R* tab_s = reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(rho_s) +
-                                  ((2 * PS * (int)sizeof(R) + 127) / 128) * 128);  // NB x TABB
-
-  auto slot_of = [&](int p) { return (p - (z0 - 1)) % NB; };
-  auto use_of = [&](int p) { return (p - (z0 - 1)) / NB; };
-  auto M = [&](int s, int i) { return reinterpret_cast<const S*>(slots + (size_t)s * SLOTB + i * POPB); };
-  auto L = [&](int s, int i) { return reinterpret_cast<const S*>(slots + (size_t)s * SLOTB + i * POPB + MB); };
-  auto Rh = [&](int s, int i) { return reinterpret_cast<const S*>(slots + (size_t)s * SLOTB + i * POPB + MB + HB); };
+  // TMA destinations want 128-byte alignment: offset the shared array itself so the compiler
+  // keeps shared-space addressing
+  unsigned char* sb = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(sb);      // NB
+  unsigned long long* empty = full + NB;                                     // NB
+  unsigned char* slots = sb + 128;
+  R* rho_s = reinterpret_cast<R*>(slots + NB * SLOTB);
+  unsigned char* tabs = reinterpret_cast<unsigned char*>(rho_s) + RHOB;      // NB x TABB
 
   if (tid == 0) {
-    for (int k = 0; k < NB; ++k) mbar_init(smem_u32(&bars[k]));
+    for (int k = 0; k < NB; ++k) {
+      mbar_init_count(smem_u32(&full[k]), 1);
+      mbar_init_count(smem_u32(&empty[k]), NCW);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     probe_cnt = 0;
     abort_flag = 0;
@@ -469,304 +493,329 @@ __global__ void __launch_bounds__(32 * (BY + 2), 2) step_tma_kernel(
     if (pq1 >= y0 && pq1 < y0 + BY && pq2 >= x0 && pq2 < x0 + BX && pq3 >= z0 && pq3 < z1)
       probe_list[atomicAdd(&probe_cnt, 1)] = tid;
   }
+  __syncthreads();
 
-  // staging of raw plane p into its slot (one thread)
-  int last_issued = z0 - 2;
-  auto issue = [&](int p) {
-    last_issued = p;
-    const int s = slot_of(p);
-    const unsigned bar = smem_u32(&bars[s]);
-    const int pg = resolve(p, a.n3, p3);
-    if (p > z1 + 1 || pg < 0) {  // nothing to stage: complete the phase without data
-      mbar_expect_tx(bar, 0);
-      return;
-    }
-    int xl = x0 - V, xr = x0 + BX;
-    const bool hl = xl >= 0 || p2, hr = xr < a.n2 || p2;
-    if (xl < 0) xl += a.n2;
-    if (xr >= a.n2) xr -= a.n2;
-    const unsigned tx_pop = (unsigned)(ROWS * BX * sizeof(S)) + (hl ? ROWS * 16u : 0u) + (hr ? ROWS * 16u : 0u);
-    const bool tab = p >= z0 && p < z1;
-    mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * sizeof(R)) : 0u));
-    unsigned char* base = slots + (size_t)s * SLOTB;
-    for (int i = 0; i < 7; ++i) {
-      const int row = y0 - 1 - xi1_of(i);
-      tma_load_4d(smem_u32(base + i * POPB), &tm_main, x0, row, pg, i, bar);
-      if (hl) tma_load_4d(smem_u32(base + i * POPB + MB), &tm_halo, xl, row, pg, i, bar);
-      if (hr) tma_load_4d(smem_u32(base + i * POPB + MB + HB), &tm_halo, xr, row, pg, i, bar);
-    }
-    if (tab) tma_load_3d(smem_u32(reinterpret_cast<unsigned char*>(tab_s) + (size_t)s * TABB), &tm_tab, 0, y0, pg, bar);
-  };
-  auto wait_plane = [&](int p) {
-    const unsigned bar = smem_u32(&bars[slot_of(p)]);
-    const unsigned parity = (unsigned)(use_of(p) & 1);
+  auto wait_bar = [&](unsigned long long* bar, unsigned parity) -> bool {
+    const unsigned b = smem_u32(bar);
     long long it = 0;
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait(b, parity)) {
       if (++it > kWaitLimit) {
         abort_flag = 1;
         a.counters[3] = 1;
-        break;
+        return false;
       }
     }
-  };
-
-  // this warp's row and this lane's nodes (fixed along q3)
-  const int q1 = y0 - 1 + w;
-  const int r1 = resolve(q1, a.n1, false);
-  const bool interior = w >= 1 && w <= BY;
-  const int c0 = lane * NPT;
-  const int q2 = x0 + c0;
-  const bool owner = interior && q1 < a.n1;
-  const bool q2lo = !p2 && q2 == 0, q2hi = !p2 && q2 + NPT - 1 == a.n2 - 1;
-
-  // pops 1 / 2 of a row: (population, staged row, factor); the pull or the q1-face rule
-  struct RowSrc { int pop1, row1, pop2, row2; R m1, m2; bool slow; };
-  auto row_src = [&](int rr1, int wr) {
-    RowSrc o{1, wr, 2, wr, R(1), R(1), false};
-    if (rr1 == 0) {
-      const int b = a.bc[0];
-      if (b == LBW_BC_FREE) { o.pop1 = 1; o.row1 = wr + 1; }
-      else { o.pop1 = 2; o.row1 = wr - 1; o.m1 = b == LBW_BC_BOUNCE ? a.damping : R(-1); }
-      if (wr == 0 || wr == ROWS - 1) o.slow = true;
-    }
-    if (rr1 == a.n1 - 1) {
-      const int b = a.bc[1];
-      if (b == LBW_BC_FREE) { o.pop2 = 2; o.row2 = wr - 1; }
-      else { o.pop2 = 1; o.row2 = wr + 1; o.m2 = b == LBW_BC_BOUNCE ? a.damping : R(-1); }
-      if (wr == 0 || wr == ROWS - 1) o.slow = true;
-    }
-    return o;
-  };
-  const RowSrc rs = row_src(r1, w);
-
-  // halo column node of a halo warp: warp 0 lane l -> (y0 + l, x0 - 1), warp BY+1 -> x0 + BX
-  const bool hcol = !interior && lane < BY;
-  const int hq1 = y0 + lane, hq2 = (w == 0) ? x0 - 1 : x0 + BX;
-  const int hr1 = resolve(hq1, a.n1, false), hr2 = resolve(hq2, a.n2, p2);
-  const RowSrc hs = row_src(hr1, lane + 1);
-  const bool hslow = hs.slow || (!p2 && hr2 >= 0 && (hr2 == 0 || hr2 == a.n2 - 1));
-  const int hrho = (lane + 1) * PW + ((w == 0) ? 1 : BX + 2);
-
-  // element of population i at staged (row, col), col in [-V, BX + V)
-  auto at = [&](int s, int i, int row, int col) -> R {
-    R v;
-    if (col < 0) v = Store<S>::ld_smem(L(s, i) + row * V + col + V);
-    else if (col >= BX) v = Store<S>::ld_smem(Rh(s, i) + row * V + col - BX);
-    else v = Store<S>::ld_smem(M(s, i) + row * BX + col);
-    return v;
-  };
-
-  // step A: populations of plane u into f, rho into rr and the rho plane
-  auto plane_A = [&](int u, R (&f)[7][NPT], R (&rr)[NPT]) {
-    const int r3 = resolve(u, a.n3, p3);
-    const int s0 = slot_of(u), sm = slot_of(u - 1), sp = slot_of(u + 1);
-    // pops 5 / 6: planes below / above, or the q3-face rule (slot, population, factor)
-    int s5 = sm, i5 = 5, s6 = sp, i6 = 6;
-    R m5 = R(1), m6 = R(1);
-    if (!p3 && r3 == 0) {
-      const int b = a.bc[4];
-      s5 = s0;
-      if (b != LBW_BC_FREE) { i5 = 6; m5 = b == LBW_BC_BOUNCE ? a.damping : R(-1); }
-    }
-    if (!p3 && r3 == a.n3 - 1) {
-      const int b = a.bc[5];
-      s6 = s0;
-      if (b != LBW_BC_FREE) { i6 = 5; m6 = b == LBW_BC_BOUNCE ? a.damping : R(-1); }
-    }
-    const R sc0 = Store<S>::kScaled ? a.w[0] : R(1), sc1 = Store<S>::kScaled ? a.w[1] : R(1);
-    if (r3 < 0 || r1 < 0) {
-#pragma unroll
-      for (int k = 0; k < NPT; ++k) rr[k] = R(0);
-    } else if (rs.slow) {
-#pragma unroll 1
-      for (int k = 0; k < NPT; ++k) {
-        R g[7];
-        pull_global(a, r1, q2 + k, r3, g);
-#pragma unroll
-        for (int m = 0; m < NPT; ++m)
-          if (m == k) {
-#pragma unroll
-            for (int i = 0; i < 7; ++i) f[i][m] = g[i];
-            rr[m] = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
-          }
-      }
-    } else {
-      R t3[NPT], t4[NPT];
-      Vec<S>::ld(M(s0, 0) + w * BX + c0, f[0]);
-      Vec<S>::ld(M(s0, rs.pop1) + rs.row1 * BX + c0, f[1]);
-      Vec<S>::ld(M(s0, rs.pop2) + rs.row2 * BX + c0, f[2]);
-      Vec<S>::ld(M(s0, 3) + w * BX + c0, t3);
-      Vec<S>::ld(M(s0, 4) + w * BX + c0, t4);
-      Vec<S>::ld(M(s5, i5) + w * BX + c0, f[5]);
-      Vec<S>::ld(M(s6, i6) + w * BX + c0, f[6]);
-      f[3][0] = lane == 0 ? Store<S>::ld_smem(L(s0, 3) + w * V + V - 1)
-                          : Store<S>::ld_smem(M(s0, 3) + w * BX + c0 - 1);
-      f[3][1] = t3[0];
-      f[4][0] = t4[1];
-      f[4][1] = lane == 31 ? Store<S>::ld_smem(Rh(s0, 4) + w * V)
-                           : Store<S>::ld_smem(M(s0, 4) + w * BX + c0 + 2);
-#pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        f[0][k] *= sc0;
-        f[1][k] *= rs.m1 * sc1;
-        f[2][k] *= rs.m2 * sc1;
-        f[3][k] *= sc1;
-        f[4][k] *= sc1;
-        f[5][k] *= m5 * sc1;
-        f[6][k] *= m6 * sc1;
-      }
-      if (q2lo) {
-        const int b = a.bc[2];
-        f[3][0] = sc1 * (b == LBW_BC_FREE ? t3[0] : (b == LBW_BC_BOUNCE ? a.damping : R(-1)) * t4[0]);
-      }
-      if (q2hi) {
-        const int b = a.bc[3];
-        f[4][1] = sc1 * (b == LBW_BC_FREE ? t4[1] : (b == LBW_BC_BOUNCE ? a.damping : R(-1)) * t3[1]);
-      }
-#pragma unroll
-      for (int k = 0; k < NPT; ++k)
-        rr[k] = ((f[0][k] + f[1][k]) + (f[2][k] + f[3][k])) + ((f[4][k] + f[5][k]) + f[6][k]);
-    }
-    R* out = rho_s + (size_t)(u & 1) * PS;
-    RVec<R>::st(out + w * PW + 2 + c0, rr);
-    if (hcol) {
-      R h = R(0);
-      if (r3 >= 0 && hr1 >= 0 && hr2 >= 0) {
-        R g[7];
-        if (hslow) {
-          pull_global(a, hr1, hr2, r3, g);
-        } else {
-          const int hw = lane + 1, hc = hq2 - x0;  // staged row and column (-1 or BX)
-          g[0] = sc0 * at(s0, 0, hw, hc);
-          g[1] = hs.m1 * sc1 * at(s0, hs.pop1, hs.row1, hc);
-          g[2] = hs.m2 * sc1 * at(s0, hs.pop2, hs.row2, hc);
-          g[3] = sc1 * at(s0, 3, hw, hc - 1);
-          g[4] = sc1 * at(s0, 4, hw, hc + 1);
-          g[5] = m5 * sc1 * at(s5, i5, hw, hc);
-          g[6] = m6 * sc1 * at(s6, i6, hw, hc);
-        }
-        h = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
-      }
-      out[hrho] = h;
-    }
-  };
-
-  // step B: collide plane z
-  auto plane_B = [&](int z, R (&fc)[7][NPT], const R (&rp)[NPT], const R (&rc)[NPT],
-                     const R (&rn)[NPT]) {
-    const R* cur = rho_s + (size_t)(z & 1) * PS + w * PW + 2 + c0;
-    R ru[NPT], rd[NPT], rl[NPT], rr[NPT];
-    RVec<R>::ld(cur + PW, ru);
-    RVec<R>::ld(cur - PW, rd);
-    rl[0] = cur[-1];
-    rl[1] = rc[0];
-    rr[0] = rc[1];
-    rr[1] = cur[2];
-    if (q2lo) rl[0] = a.s2lo * rc[0];
-    if (q2hi) rr[1] = a.s2hi * rc[1];
-    const R* T = tab_s + (size_t)slot_of(z) * (TABB / sizeof(R)) + (w - 1) * T_SLOTS;
-    R c[T_SLOTS];
-#pragma unroll
-    for (int k = 0; k < T_SLOTS; k += 4) {
-      if (sizeof(R) == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(T + k);
-        c[k] = v.x; c[k + 1] = v.y; c[k + 2] = v.z; c[k + 3] = v.w;
-      } else {
-        const double2 v0 = *reinterpret_cast<const double2*>(T + k);
-        const double2 v1 = *reinterpret_cast<const double2*>(T + k + 2);
-        c[k] = v0.x; c[k + 1] = v0.y; c[k + 2] = v1.x; c[k + 3] = v1.y;
-      }
-    }
-    const R half = R(0.5);
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      const R rho = rc[k];
-      const R D1 = c[T_A1P] * ru[k] - c[T_A1M] * rd[k] + c[T_C13P] * rn[k] - c[T_C13M] * rp[k] + c[T_S1] * rho;
-      const R D3 = c[T_B13P] * ru[k] - c[T_B13M] * rd[k] + c[T_C33P] * rn[k] - c[T_C33M] * rp[k] + c[T_S3] * rho;
-      const R D2 = c[T_H22] * (rr[k] - rl[k]);
-      const R j1 = (fc[1][k] - fc[2][k]) + half * (c[T_MG1] * rho - D1);
-      const R j2 = (fc[3][k] - fc[4][k]) - half * D2;
-      const R j3 = (fc[5][k] - fc[6][k]) + half * (c[T_MG3] * rho - D3);
-      const R e = a.cs2 * rho;
-      fc[0][k] = a.two_w0 * rho - fc[0][k];
-      fc[1][k] = e + j1 - fc[1][k];
-      fc[2][k] = e - j1 - fc[2][k];
-      fc[3][k] = e + j2 - fc[3][k];
-      fc[4][k] = e - j2 - fc[4][k];
-      fc[5][k] = e + j3 - fc[5][k];
-      fc[6][k] = e - j3 - fc[6][k];
-    }
-    S* dst = a.fout + node(q1, q2, z, a.n1, a.n2);
-#pragma unroll
-    for (int i = 0; i < 7; ++i) {
-      if (Store<S>::kScaled) {
-#pragma unroll
-        for (int k = 0; k < NPT; ++k) fc[i][k] *= a.inv_w[i];
-      }
-      Vec<S>::st(dst + (long long)i * a.nn, fc[i]);
-    }
-    if (probe_cnt > 0 && t_sample < (unsigned long long)a.cap) {
-      for (int s2 = 0; s2 < probe_cnt; ++s2) {
-        const int k = probe_list[s2];
-        const int dq = a.probe_q[3 * k + 1] - q2;
-        if (a.probe_q[3 * k] == q1 && dq >= 0 && dq < NPT && a.probe_q[3 * k + 2] == z)
-          a.series[(long long)k * a.cap + t_sample] = (double)(dq == 0 ? rc[0] : rc[1]) * (double)c[T_INVSG];
-      }
-    }
-  };
-
-  // prologue: stage raw planes z0 - 1 .. z0 + 1 + D; rho of plane z0 - 1 (own column, whose
-  // pop 5 lies in the unstaged plane z0 - 2) from global memory; plane z0 from the slots
-  if (tid == 0)
-    for (int p = z0 - 1; p <= z0 + 1 + D; ++p) issue(p);
-  R fA[7][NPT], fB[7][NPT];
-  R rA[NPT], rB[NPT], rC[NPT];
-  {
-    const int u = z0 - 1, r3 = resolve(u, a.n3, p3);
-#pragma unroll 1
-    for (int k = 0; k < NPT; ++k) {
-      R v = R(0);
-      if (owner && r3 >= 0) {
-        R g[7];
-        pull_global(a, r1, q2 + k, r3, g);
-        v = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
-      }
-      if (k == 0) rA[0] = v; else rA[1] = v;
-    }
-  }
-  wait_plane(z0 - 1);
-  wait_plane(z0);
-  wait_plane(z0 + 1);
-  plane_A(z0, fA, rB);
-
-  auto iter = [&](int z, R (&fc)[7][NPT], R (&fn)[7][NPT], R (&rp)[NPT], R (&rc)[NPT],
-                  R (&rn)[NPT]) {
-    wait_plane(z + 2);
-    __syncthreads();  // all reads of raw plane z - 1 and of the rho plane z + 1 (&1) are done
-    if (abort_flag) return false;
-    if (tid == 0) issue(z + 2 + D);
-    plane_A(z + 1, fn, rn);
-    if (owner) plane_B(z, fc, rp, rc, rn);
     return true;
   };
-  int z = z0;
-  bool ok = true;
-  for (; ok && z + 1 < z1; z += 2) {
-    ok = iter(z, fA, fB, rA, rB, rC);
-    if (ok) ok = iter(z + 1, fB, fA, rB, rC, rA);
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      const R t = rA[k];
-      rA[k] = rC[k];
-      rB[k] = t;
-    }
-  }
-  if (ok && z < z1) ok = iter(z, fA, fB, rA, rB, rC);
 
-  // drain: every staged plane has landed before the CTA exits (bounded)
+  if (w == ROWS) {  // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int xl = x0 - V, xr = x0 + BX;
+      const bool hl = xl >= 0 || p2, hr = xr < a.n2 || p2;
+      if (xl < 0) xl += a.n2;
+      if (xr >= a.n2) xr -= a.n2;
+      const unsigned tx_pop = (unsigned)(ROWS * BX * ES) + (hl ? ROWS * 16u : 0u) + (hr ? ROWS * 16u : 0u);
+      int s = 0, use = 0;
+      int issued = z0 - 2;
+      for (int p = z0 - 1; p <= z1 + 1; ++p) {
+        if (use > 0 && !wait_bar(&empty[s], (unsigned)((use - 1) & 1))) break;
+        const unsigned bar = smem_u32(&full[s]);
+        const int pg = resolve(p, a.n3, p3);
+        if (pg < 0) {
+          mbar_expect_tx(bar, 0);
+        } else {
+          const bool tab = p >= z0 && p < z1;
+          mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
+          unsigned char* base = slots + s * SLOTB;
+#pragma unroll 1
+          for (int i = 0; i < 7; ++i) {
+            const int row = y0 - 1 - xi1_of(i);
+            tma_load_4d(smem_u32(base + i * POPB), &tm_main, x0, row, pg, i, bar);
+            if (hl) tma_load_4d(smem_u32(base + i * POPB + MB), &tm_halo, xl, row, pg, i, bar);
+            if (hr) tma_load_4d(smem_u32(base + i * POPB + MB + HB), &tm_halo, xr, row, pg, i, bar);
+          }
+          if (tab) tma_load_3d(smem_u32(tabs + s * TABB), &tm_tab, 0, y0, pg, bar);
+        }
+        issued = p;
+        if (++s == NB) { s = 0; ++use; }
+      }
+      // drain: the last NB staged planes have landed before the CTA exits (bounded)
+      for (int p = max(z0 - 1, issued - NB + 1); p <= issued; ++p) {
+        const int k = p - (z0 - 1);
+        wait_bar(&full[k % NB], (unsigned)((k / NB) & 1));
+      }
+    }
+  } else {  // ------------------------------------------------------------------- consumers
+    const int q1 = y0 - 1 + w;
+    const int r1 = resolve(q1, a.n1, false);
+    const bool interior = w >= 1 && w <= BY;
+    const int c0 = lane * NPT;
+    const int q2 = x0 + c0;
+    const bool owner = interior && q1 < a.n1;
+    const bool q2lo = !p2 && q2 == 0, q2hi = !p2 && q2 + NPT - 1 == a.n2 - 1;
+    const R sc0 = Store<S>::kScaled ? a.w[0] : R(1), sc1 = Store<S>::kScaled ? a.w[1] : R(1);
+
+    // byte offsets within a slot of this lane's vectors: pops 0, 3, 4, 5, 6 at (w, c0);
+    // pops 1 / 2 at the pull or at the q1-face rule
+    const int own = w * BX * ES + c0 * ES;
+    int o1 = POPB + own, o2 = 2 * POPB + own;
+    R m1 = sc1, m2 = sc1;
+    bool slow = false;
+    if (r1 == 0) {
+      const int b = a.bc[0];
+      if (b == LBW_BC_FREE) o1 = POPB + own + BX * ES;
+      else { o1 = 2 * POPB + own - BX * ES; m1 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
+      if (!interior) slow = true;
+    }
+    if (r1 == a.n1 - 1) {
+      const int b = a.bc[1];
+      if (b == LBW_BC_FREE) o2 = 2 * POPB + own - BX * ES;
+      else { o2 = POPB + own + BX * ES; m2 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
+      if (!interior) slow = true;
+    }
+    // pop 3 of node c0 reads column c0 - 1 (left halo box for lane 0), pop 4 of node c0 + 1
+    // reads column c0 + 2 (right halo box for lane 31)
+    const int o3e = lane == 0 ? 3 * POPB + MB + w * 16 + (V - 1) * ES : 3 * POPB + own - ES;
+    const int o4e = lane == 31 ? 4 * POPB + MB + HB + w * 16 : 4 * POPB + own + 2 * ES;
+
+    // halo column node of a halo warp: warp 0 lane l -> (y0 + l, x0 - 1), warp BY+1 -> x0 + BX
+    const bool hcol = !interior && lane < BY;
+    const int hq1 = y0 + lane, hq2 = (w == 0) ? x0 - 1 : x0 + BX;
+    const int hr1 = resolve(hq1, a.n1, false), hr2 = resolve(hq2, a.n2, p2);
+    int h0 = 0, h1 = 0, h2 = 0, h3 = 0, h4 = 0, h56 = 0;  // byte offsets in a slot
+    R hm1 = sc1, hm2 = sc1;
+    bool hslow = false;
+    if (hcol) {
+      const int hw = lane + 1;
+      // column -1 lives in the left halo box (index V - 1), column BX in the right one (0)
+      const int hbox = (w == 0) ? MB : MB + HB, hcolb = (w == 0) ? (V - 1) * ES : 0;
+      auto hat = [&](int pop, int row) { return pop * POPB + hbox + row * 16 + hcolb; };
+      h0 = hat(0, hw);
+      h1 = hat(1, hw);
+      h2 = hat(2, hw);
+      h56 = hat(0, hw) - 0 * POPB;  // pop offset added per plane
+      // pop 3 from column -2 / BX - 1, pop 4 from column 0 / BX + 1
+      h3 = (w == 0) ? 3 * POPB + MB + hw * 16 + (V - 2) * ES : 3 * POPB + hw * BX * ES + (BX - 1) * ES;
+      h4 = (w == 0) ? 4 * POPB + hw * BX * ES : 4 * POPB + MB + HB + hw * 16 + ES;
+      if (hr1 == 0) {
+        const int b = a.bc[0];
+        if (b == LBW_BC_FREE) h1 = hat(1, hw + 1);
+        else { h1 = hat(2, hw - 1); hm1 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
+      }
+      if (hr1 == a.n1 - 1) {
+        const int b = a.bc[1];
+        if (b == LBW_BC_FREE) h2 = hat(2, hw - 1);
+        else { h2 = hat(1, hw + 1); hm2 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
+      }
+      hslow = !p2 && hr2 >= 0 && (hr2 == 0 || hr2 == a.n2 - 1);
+    }
+    const int hrho = (lane + 1) * PW + ((w == 0) ? 1 : BX + 2);
+
+    R fA[7][NPT], fB[7][NPT], rA[NPT], rB[NPT], rC[NPT];
+    const long long n12 = (long long)a.n1 * a.n2;
+    S* const dst_z0 = a.fout + node(owner ? q1 : 0, q2, z0, a.n1, a.n2);
+
+    // step A of pulled plane u: populations into f, rho into rr and the rho plane
+#define LBW_STEP_A(u, f, rr, slm, sl0, slp, rbu)                                                  \
+    do {                                                                                          \
+      const int r3_ = resolve((u), a.n3, p3);                                                     \
+      const unsigned char* S0 = slots + (sl0) * SLOTB;                                            \
+      const unsigned char* Sm = slots + (slm) * SLOTB;                                            \
+      const unsigned char* Sp = slots + (slp) * SLOTB;                                            \
+      const unsigned char* B5 = Sm + 5 * POPB;                                                    \
+      const unsigned char* B6 = Sp + 6 * POPB;                                                    \
+      R m5_ = sc1, m6_ = sc1;                                                                     \
+      if (!p3 && r3_ == 0) {                                                                      \
+        const int b_ = a.bc[4];                                                                   \
+        if (b_ == LBW_BC_FREE) B5 = S0 + 5 * POPB;                                                \
+        else { B5 = S0 + 6 * POPB; m5_ = sc1 * (b_ == LBW_BC_BOUNCE ? a.damping : R(-1)); }       \
+      }                                                                                           \
+      if (!p3 && r3_ == a.n3 - 1) {                                                               \
+        const int b_ = a.bc[5];                                                                   \
+        if (b_ == LBW_BC_FREE) B6 = S0 + 6 * POPB;                                                \
+        else { B6 = S0 + 5 * POPB; m6_ = sc1 * (b_ == LBW_BC_BOUNCE ? a.damping : R(-1)); }       \
+      }                                                                                           \
+      if (r3_ < 0 || r1 < 0) {                                                                    \
+        rr[0] = R(0); rr[1] = R(0);                                                               \
+      } else if (slow) {                                                                          \
+        _Pragma("unroll 1") for (int k_ = 0; k_ < NPT; ++k_) {                                  \
+          R g_[7];                                                                                \
+          pull_global(a, r1, q2 + k_, r3_, g_);                                                   \
+          const R s_ = ((g_[0] + g_[1]) + (g_[2] + g_[3])) + ((g_[4] + g_[5]) + g_[6]);           \
+          if (k_ == 0) { for (int i_ = 0; i_ < 7; ++i_) f[i_][0] = g_[i_]; rr[0] = s_; }          \
+          else { for (int i_ = 0; i_ < 7; ++i_) f[i_][1] = g_[i_]; rr[1] = s_; }                  \
+        }                                                                                         \
+      } else {                                                                                    \
+        R t3_[NPT], t4_[NPT];                                                                     \
+        Vec<S>::ld(reinterpret_cast<const S*>(S0 + own), f[0]);                                   \
+        Vec<S>::ld(reinterpret_cast<const S*>(S0 + o1), f[1]);                                    \
+        Vec<S>::ld(reinterpret_cast<const S*>(S0 + o2), f[2]);                                    \
+        Vec<S>::ld(reinterpret_cast<const S*>(S0 + 3 * POPB + own), t3_);                         \
+        Vec<S>::ld(reinterpret_cast<const S*>(S0 + 4 * POPB + own), t4_);                         \
+        Vec<S>::ld(reinterpret_cast<const S*>(B5 + own), f[5]);                                   \
+        Vec<S>::ld(reinterpret_cast<const S*>(B6 + own), f[6]);                                   \
+        f[3][0] = sc1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + o3e));                  \
+        f[3][1] = sc1 * t3_[0];                                                                   \
+        f[4][0] = sc1 * t4_[1];                                                                   \
+        f[4][1] = sc1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + o4e));                  \
+        _Pragma("unroll") for (int k_ = 0; k_ < NPT; ++k_) {                                    \
+          f[0][k_] *= sc0; f[1][k_] *= m1; f[2][k_] *= m2; f[5][k_] *= m5_; f[6][k_] *= m6_;      \
+        }                                                                                         \
+        if (q2lo) {                                                                               \
+          const int b_ = a.bc[2];                                                                 \
+          f[3][0] = sc1 * (b_ == LBW_BC_FREE ? t3_[0] : (b_ == LBW_BC_BOUNCE ? a.damping : R(-1)) * t4_[0]); \
+        }                                                                                         \
+        if (q2hi) {                                                                               \
+          const int b_ = a.bc[3];                                                                 \
+          f[4][1] = sc1 * (b_ == LBW_BC_FREE ? t4_[1] : (b_ == LBW_BC_BOUNCE ? a.damping : R(-1)) * t3_[1]); \
+        }                                                                                         \
+        _Pragma("unroll") for (int k_ = 0; k_ < NPT; ++k_)                                      \
+          rr[k_] = ((f[0][k_] + f[1][k_]) + (f[2][k_] + f[3][k_])) + ((f[4][k_] + f[5][k_]) + f[6][k_]); \
+      }                                                                                           \
+      R* out_ = rho_s + (rbu) * PS;                                                               \
+      RVec<R>::st(out_ + w * PW + 2 + c0, rr);                                                    \
+      if (hcol) {                                                                                 \
+        R h_ = R(0);                                                                              \
+        if (r3_ >= 0 && hr1 >= 0 && hr2 >= 0) {                                                   \
+          R g_[7];                                                                                \
+          if (hslow) {                                                                            \
+            pull_global(a, hr1, hr2, r3_, g_);                                                    \
+          } else {                                                                                \
+            g_[0] = sc0 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h0));                 \
+            g_[1] = hm1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h1));                 \
+            g_[2] = hm2 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h2));                 \
+            g_[3] = sc1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h3));                 \
+            g_[4] = sc1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h4));                 \
+            g_[5] = m5_ * Store<S>::ld_smem(reinterpret_cast<const S*>(B5 + h56));                \
+            g_[6] = m6_ * Store<S>::ld_smem(reinterpret_cast<const S*>(B6 + h56));                \
+          }                                                                                       \
+          h_ = ((g_[0] + g_[1]) + (g_[2] + g_[3])) + ((g_[4] + g_[5]) + g_[6]);                   \
+        }                                                                                         \
+        out_[hrho] = h_;                                                                          \
+      }                                                                                           \
+    } while (0)
+
+    // step B: collide plane z with populations fc, rho (rp, rc, rn)
+#define LBW_STEP_B(zc, fc, rp, rc, rn, slz, rbz)                                                   \
+    do {                                                                                          \
+      const R* cur_ = rho_s + (rbz) * PS + w * PW + 2 + c0;                                       \
+      R ru_[NPT], rd_[NPT];                                                                       \
+      RVec<R>::ld(cur_ + PW, ru_);                                                                \
+      RVec<R>::ld(cur_ - PW, rd_);                                                                \
+      const R rl0_ = q2lo ? a.s2lo * rc[0] : cur_[-1];                                            \
+      const R rr1_ = q2hi ? a.s2hi * rc[1] : cur_[2];                                             \
+      const R rl_[NPT] = {rl0_, rc[0]}, rrr_[NPT] = {rc[1], rr1_};                                \
+      const unsigned char* T_ = tabs + (slz) * TABB + (w - 1) * T_SLOTS * RS;                    \
+      R c_[T_SLOTS];                                                                              \
+      _Pragma("unroll") for (int k_ = 0; k_ < T_SLOTS; k_ += 4) {                               \
+        if (RS == 4) {                                                                            \
+          const float4 v_ = lds<float4>(T_, k_ * RS);                                             \
+          c_[k_] = v_.x; c_[k_ + 1] = v_.y; c_[k_ + 2] = v_.z; c_[k_ + 3] = v_.w;                 \
+        } else {                                                                                  \
+          const double2 v0_ = lds<double2>(T_, k_ * RS), v1_ = lds<double2>(T_, (k_ + 2) * RS);   \
+          c_[k_] = v0_.x; c_[k_ + 1] = v0_.y; c_[k_ + 2] = v1_.x; c_[k_ + 3] = v1_.y;             \
+        }                                                                                         \
+      }                                                                                           \
+      _Pragma("unroll") for (int k_ = 0; k_ < NPT; ++k_) {                                      \
+        const R rho_ = rc[k_];                                                                    \
+        const R D1_ = c_[T_A1P] * ru_[k_] - c_[T_A1M] * rd_[k_] + c_[T_C13P] * rn[k_] -           \
+                      c_[T_C13M] * rp[k_] + c_[T_S1] * rho_;                                      \
+        const R D3_ = c_[T_B13P] * ru_[k_] - c_[T_B13M] * rd_[k_] + c_[T_C33P] * rn[k_] -         \
+                      c_[T_C33M] * rp[k_] + c_[T_S3] * rho_;                                      \
+        const R D2_ = c_[T_H22] * (rrr_[k_] - rl_[k_]);                                           \
+        const R j1_ = (fc[1][k_] - fc[2][k_]) + R(0.5) * (c_[T_MG1] * rho_ - D1_);                \
+        const R j2_ = (fc[3][k_] - fc[4][k_]) - R(0.5) * D2_;                                     \
+        const R j3_ = (fc[5][k_] - fc[6][k_]) + R(0.5) * (c_[T_MG3] * rho_ - D3_);                \
+        const R e_ = a.cs2 * rho_;                                                                \
+        fc[0][k_] = a.two_w0 * rho_ - fc[0][k_];                                                  \
+        fc[1][k_] = e_ + j1_ - fc[1][k_];                                                         \
+        fc[2][k_] = e_ - j1_ - fc[2][k_];                                                         \
+        fc[3][k_] = e_ + j2_ - fc[3][k_];                                                         \
+        fc[4][k_] = e_ - j2_ - fc[4][k_];                                                         \
+        fc[5][k_] = e_ + j3_ - fc[5][k_];                                                         \
+        fc[6][k_] = e_ - j3_ - fc[6][k_];                                                         \
+      }                                                                                           \
+      S* dst_ = dst_z0 + (long long)((zc) - z0) * n12;                                            \
+      _Pragma("unroll") for (int i_ = 0; i_ < 7; ++i_) {                                        \
+        if (Store<S>::kScaled) { fc[i_][0] *= a.inv_w[i_]; fc[i_][1] *= a.inv_w[i_]; }            \
+        Vec<S>::st(dst_, fc[i_]);                                                                 \
+        dst_ += a.nn;                                                                             \
+      }                                                                                           \
+      if (probe_cnt > 0 && t_sample < (unsigned long long)a.cap) {                                \
+        for (int s2_ = 0; s2_ < probe_cnt; ++s2_) {                                               \
+          const int k_ = probe_list[s2_];                                                         \
+          const int dq_ = a.probe_q[3 * k_ + 1] - q2;                                             \
+          if (a.probe_q[3 * k_] == q1 && dq_ >= 0 && dq_ < NPT && a.probe_q[3 * k_ + 2] == (zc))   \
+            a.series[(long long)k_ * a.cap + t_sample] =                                          \
+                (double)(dq_ == 0 ? rc[0] : rc[1]) * (double)c_[T_INVSG];                         \
+        }                                                                                         \
+      }                                                                                           \
+    } while (0)
+
+    // rho of plane z0 - 1 (own column; its pop 5 lies in the unstaged plane z0 - 2)
+    {
+      const int r3 = resolve(z0 - 1, a.n3, p3);
+      for (int k = 0; k < NPT; ++k) {
+        R v = R(0);
+        if (owner && r3 >= 0) {
+          R g[7];
+          pull_global(a, r1, q2 + k, r3, g);
+          v = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+        }
+        if (k == 0) rA[0] = v; else rA[1] = v;
+      }
+    }
+    bool ok = wait_bar(&full[0], 0) && wait_bar(&full[1], 0) && wait_bar(&full[2], 0);
+    if (ok) LBW_STEP_A(z0, fA, rB, 0, 1, 2, 0);
+    if (lane == 0) mbar_arrive(smem_u32(&empty[0]));  // raw plane z0 - 1 is no longer needed
+    named_sync(1, NCW * 32);
+    int z = z0;
+    // slots of raw planes z, z + 1, z + 2 (plane z0 - 1 sits in slot 0) and the fill count of
+    // plane z + 2's slot, advanced plane by plane
+    // rho planes rotate through three buffers: a warp writing plane z + 1's buffer has passed
+    // the barrier that follows every read of that buffer (plane z - 2)
+    int sz = 1, s1 = 2, s2 = 3, u2 = 0, rbz = 0, rb1 = 1;
+#define LBW_ADVANCE()                                                                             \
+    do {                                                                                          \
+      rbz = rb1;                                                                                  \
+      rb1 = rb1 == 2 ? 0 : rb1 + 1;                                                               \
+      sz = s1;                                                                                    \
+      s1 = s2;                                                                                    \
+      s2 = s2 == NB - 1 ? 0 : s2 + 1;                                                             \
+      if (s2 == 0) ++u2;                                                                          \
+    } while (0)
+    // iteration z: raw plane z + 2 in, A(z + 1), barrier, B(z), release raw plane z
+#define LBW_ITER(zz, fc, fn, rp, rc, rn)                                                          \
+    do {                                                                                          \
+      if (!abort_flag && !wait_bar(&full[s2], (unsigned)(u2 & 1))) ok = false;                    \
+      if (ok && !abort_flag) LBW_STEP_A((zz) + 1, fn, rn, sz, s1, s2, rb1);                       \
+      named_sync(1, NCW * 32);                                                                    \
+      if (abort_flag) ok = false;                                                                 \
+      if (ok && owner) LBW_STEP_B((zz), fc, rp, rc, rn, sz, rbz);                                 \
+      /* raw plane zz (pop 5 of A(zz + 1), coefficient rows of B(zz)) is no longer needed */      \
+      if (lane == 0) mbar_arrive(smem_u32(&empty[sz]));                                           \
+      LBW_ADVANCE();                                                                              \
+    } while (0)
+    for (; ok && z + 1 < z1; z += 2) {
+      LBW_ITER(z, fA, fB, rA, rB, rC);
+      if (!ok) break;
+      LBW_ITER(z + 1, fB, fA, rB, rC, rA);
+      // next pair expects rho(z+1), rho(z+2) in rA, rB
+      for (int k = 0; k < NPT; ++k) {
+        const R t = rA[k];
+        rA[k] = rC[k];
+        rB[k] = t;
+      }
+    }
+    if (ok && z < z1) LBW_ITER(z, fA, fB, rA, rB, rC);
+#undef LBW_ITER
+#undef LBW_ADVANCE
+#undef LBW_STEP_A
+#undef LBW_STEP_B
+  }
+
   __syncthreads();
   if (tid == 0) {
-    for (int p = max(z0 - 1, last_issued - NB + 1); p <= last_issued; ++p) wait_plane(p);
     __threadfence();
     unsigned int ticket = atomicAdd(reinterpret_cast<unsigned int*>(&a.counters[2]), 1u);
     if (ticket == a.nblocks - 1) {
@@ -815,7 +864,7 @@ constexpr size_t tma_smem_bytes() {
   constexpr int TABB = ((BY * T_SLOTS * (int)sizeof(R)) + 127) / 128 * 128;
   return 128 /* alignment slack */ + 128 /* barriers */ +
          (size_t)NB * TmaLayout<BY>::template slot_bytes<S>() +
-         ((2 * PS * sizeof(R) + 127) / 128) * 128 + (size_t)NB * TABB;
+         ((3 * PS * sizeof(R) + 127) / 128) * 128 + (size_t)NB * TABB;  // see step_tma_kernel
 }
 
 template <typename S>
@@ -824,7 +873,7 @@ cudaError_t launch_step_t(Grid* g, int src) {
   StepArgs<S> a = make_args<S>(g, src);
   if (g->tma_by > 0) {
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(g->tmaps);
-    const dim3 block(32, g->tma_by + 2);
+    const dim3 block(32, g->tma_by + 3);
     if (g->tma_by == 7)
       step_tma_kernel<S, 7><<<g->grid_dim, block, tma_smem_bytes<S, 7>(), g->stream>>>(a, m[2 * src], m[2 * src + 1], m[4]);
     else
@@ -1146,7 +1195,7 @@ void step_launch_shape(Grid* g) {
     const int bys[2] = {4, 7};
     double best = 1e300;
     for (int c = 0; c < 2; ++c) {
-      const int by = bys[c], threads = 32 * (by + 2);
+      const int by = bys[c], threads = 32 * (by + 3);
       if ((long long)smem[c] > smem_max || regs[c] > 255) continue;
       const int rr = (regs[c] + 7) & ~7;
       int per_sm = std::min<int>(2048 / threads, (int)((228LL * 1024) / (smem[c] + 1024)));
