@@ -135,6 +135,24 @@ lbw_status lbw_spectrum_series(const double* host_x, int64_t T, int32_t n_series
                                void* stream, double* host_freq, double* host_amp,
                                int32_t* host_n_found);
 
+/* The same estimator for callers that must not allocate device memory -- for example a host
+ * application whose own allocator has reserved the device memory, or a latency-critical loop
+ * that cannot afford the synchronisation an allocation may cause.  The paper has no
+ * counterpart: this is a deployment variant of lbw_spectrum_series.
+ *  - dev_x: T doubles in device memory owned by the caller (one series, 4 <= T <= 16384;
+ *    larger T is rejected with LBW_EINVAL).  host_freq / host_amp: room for k values;
+ *    *host_n_found: how many.  k in [1, 64].
+ *  - All workspace lives in one fixed device array of about 2.6 MB inside the library, which
+ *    every GPU that loads the library holds until the process exits.  No call here allocates
+ *    or frees device memory.
+ *  - The first call on a device (with that device current) looks up the array's device
+ *    address; make that first call before any stream capture.
+ *  - Every call on a device shares the array and leaves its contents behind; calls whose work
+ *    overlaps on the GPU (different streams, no ordering between them) race.  The call
+ *    synchronises `stream` before returning. */
+lbw_status lbw_spectrum_series_static(const double* dev_x, int64_t T, int32_t k, void* stream,
+                                      double* host_freq, double* host_amp, int32_t* host_n_found);
+
 /* P = rho / sqrt(g) of the current state (rho = sum of the stored post-collision
  * populations; the relaxation conserves it), N doubles in the layout above. */
 lbw_status lbw_get_field(lbw_grid* g, double* host_P);

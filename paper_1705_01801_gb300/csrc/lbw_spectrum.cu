@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "lbw_internal.h"
@@ -302,3 +303,108 @@ lbw_status spectrum_device(const double* d_x, int64_t T, int32_t n_series, int32
 }
 
 }  // namespace lbw
+
+// ---------------------------------------------------------------- no-allocation variant -----
+//
+// lbw_spectrum_series_static: the estimator above on a caller-owned device series, with all of
+// its workspace in one file-scope device array instead of stream-ordered allocations, for
+// callers that must not allocate device memory.  The array is sized for series of up to
+// kStaticMaxT samples and is held by every GPU that loads the library until the process exits.
+
+namespace lbw {
+namespace {
+
+constexpr int64_t kStaticMaxT = 16384;
+
+constexpr size_t round16(size_t n) { return (n + 15) / 16 * 16; }
+constexpr size_t static_scratch_bytes() {
+  // same layout as spectrum_device for T = kStaticMaxT (M = 4 T rounded up to a power of two)
+  return round16(4 * 8) + 2 * round16((size_t)4 * kStaticMaxT * 16) + round16(kStaticMaxT * 8) +
+         round16(((size_t)4 * kStaticMaxT / 2 + 1) * 8) + round16(((size_t)4 * kStaticMaxT / 4 + 1) * 8) +
+         round16(8) + round16(64 * 8) + round16(8) + round16(64 * 8) + round16(64 * 8);
+}
+
+}  // namespace
+}  // namespace lbw
+
+// The workspace.  In host code this name is only a host-side handle: its device address comes
+// from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_spectrum_scratch[lbw::static_scratch_bytes()];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_addr[256] = {nullptr};
+}  // namespace
+
+extern "C" lbw_status lbw_spectrum_series_static(const double* dev_x, int64_t T, int32_t k,
+                                                 void* stream, double* host_freq, double* host_amp,
+                                                 int32_t* host_n_found) {
+  using namespace lbw;
+  if (!dev_x || !host_freq || !host_amp || !host_n_found) return fail(LBW_EINVAL, "NULL argument");
+  if (T < 4 || T > kStaticMaxT)
+    return fail(LBW_EINVAL, "lbw_spectrum_series_static: T must be in [4, " + std::to_string(kStaticMaxT) +
+                                "] (the fixed workspace holds " + std::to_string(kStaticMaxT) + " samples)");
+  if (k < 1 || k > 64) return fail(LBW_EINVAL, "1 <= k <= 64");
+  int dev = 0;
+  LBW_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(LBW_EINVAL, "device ordinal out of range");
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {  // first call on this device: resolve the array's device address
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_spectrum_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_spectrum_scratch)");
+      g_static_addr[dev] = ptr;
+    }
+    base = static_cast<unsigned char*>(g_static_addr[dev]);
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  long long M = 1;
+  while (M < 4 * T) M <<= 1;
+  unsigned char* p = base;
+  auto take = [&](size_t n) { unsigned char* q = p; p += round16(n); return q; };
+  double* stats = (double*)take(4 * 8);
+  double2* A = (double2*)take((size_t)4 * kStaticMaxT * 16);
+  double2* B = (double2*)take((size_t)4 * kStaticMaxT * 16);
+  double* xw = (double*)take((size_t)kStaticMaxT * 8);
+  double* P = (double*)take(((size_t)4 * kStaticMaxT / 2 + 1) * 8);
+  long long* cand = (long long*)take(((size_t)4 * kStaticMaxT / 4 + 1) * 8);
+  unsigned long long* count = (unsigned long long*)take(8);
+  long long* chosen = (long long*)take(64 * 8);
+  int* n_chosen = (int*)take(8);
+  double* freq = (double*)take(64 * 8);
+  double* amp = (double*)take(64 * 8);
+
+  // the candidate counter is the only value read before it is written; the array keeps the
+  // previous call's contents
+  cudaError_t e = cudaMemsetAsync(count, 0, 8, s);
+  const int blocks = 152 * 4;
+  if (e == cudaSuccess) {
+    stats_kernel<<<1, 1024, 0, s>>>(dev_x, T, 1, T, stats);
+    window_kernel<<<blocks, 256, 0, s>>>(dev_x, T, 1, T, stats, M, A, xw);
+    double2 *in = A, *out = B;
+    for (long long ns = 1; ns < M; ns <<= 1) {
+      stockham_kernel<<<blocks, 256, 0, s>>>(in, out, M, ns);
+      std::swap(in, out);
+    }
+    power_kernel<<<blocks, 256, 0, s>>>(in, M, P);
+    max_kernel<<<1, 1024, 0, s>>>(P, M, stats);
+    candidates_kernel<<<blocks, 256, 0, s>>>(P, M, stats, 1e-3, cand, count);
+    select_kernel<<<1, 1024, 0, s>>>(P, cand, count, k, chosen, n_chosen);
+    refine_kernel<<<k, kThreads, 0, s>>>(xw, T, P, M, chosen, n_chosen, stats, freq, amp);
+    e = cudaGetLastError();
+  }
+  int nfound = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nfound, n_chosen, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && nfound > 0) {
+    e = cudaMemcpyAsync(host_freq, freq, sizeof(double) * nfound, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_amp, amp, sizeof(double) * nfound, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "lbw_spectrum_series_static");
+  *host_n_found = nfound;
+  return LBW_OK;
+}
+

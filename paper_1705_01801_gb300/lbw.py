@@ -20,7 +20,7 @@ STATUS_NAMES = ["LBW_OK", "LBW_EINVAL", "LBW_ENOMEM", "LBW_ECUDA", "LBW_EUNSTABL
 
 # every symbol the header declares (checked by tests/test_abi.py)
 EXPORTS = ["lbw_create_grid", "lbw_init", "lbw_step", "lbw_probe", "lbw_probe_read",
-           "lbw_spectrum", "lbw_spectrum_series", "lbw_get_field", "lbw_get_populations",
+           "lbw_spectrum", "lbw_spectrum_series", "lbw_spectrum_series_static", "lbw_get_field", "lbw_get_populations",
            "lbw_set_populations", "lbw_step_count", "lbw_destroy", "lbw_last_error"]
 
 
@@ -64,6 +64,7 @@ def lib():
                 "lbw_probe_read": (st, [vp, dp, i64, ctypes.POINTER(i64)]),
                 "lbw_spectrum": (st, [vp, i32, i32, dp, dp, ip]),
                 "lbw_spectrum_series": (st, [dp, i64, i32, i32, vp, dp, dp, ip]),
+                "lbw_spectrum_series_static": (st, [vp, i64, i32, vp, dp, dp, ip]),
                 "lbw_get_field": (st, [vp, dp]),
                 "lbw_get_populations": (st, [vp, dp]),
                 "lbw_set_populations": (st, [vp, dp]),
@@ -170,6 +171,17 @@ def lbw_spectrum_series(x, k, stream=None):
     n = np.zeros(ns, dtype=np.int32)
     _check(lib().lbw_spectrum_series(_dp(x), T, ns, int(k), stream, _dp(f), _dp(a), _ip(n)))
     return [(f[j, : n[j]], a[j, : n[j]]) for j in range(ns)]
+
+
+def lbw_spectrum_series_static(dev_ptr, T, k, stream=None):
+    """Spectrum of T doubles already in device memory at dev_ptr, using the library's fixed
+    workspace (no device allocation); returns (freq, amp)."""
+    f = np.zeros(k)
+    a = np.zeros(k)
+    n = ctypes.c_int32()
+    _check(lib().lbw_spectrum_series_static(ctypes.c_void_p(dev_ptr), int(T), int(k), stream,
+                                            _dp(f), _dp(a), ctypes.byref(n)))
+    return f[: n.value], a[: n.value]
 
 
 def lbw_get_field(grid, shape):
