@@ -248,16 +248,7 @@ def main():
     kernel_ms = sum(step_ms) / (args.steps * lbm_steps)
     achieved = spec.nodes * bytes_per_node / (kernel_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            with open(tpath) as fh:
-                tj = json.load(fh)
-            if tj.get("kernel_hash") == lbw_kernel_hash():
-                traffic = tj["bytes_per_launch_full_size"]
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic()
 
     # ---- end to end through the C ABI with host buffers
     host_pulses = np.ascontiguousarray(wl.pulses)
@@ -317,7 +308,7 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "step_kernel<float>", "peak_source": peak_kind,
+                     "kernel": "step_tma_kernel<float, 7>", "peak_source": peak_kind,
                      "bytes_per_node": bytes_per_node, "kernel_us": kernel_ms * 1e3},
         "cpu_baseline": base,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
@@ -332,11 +323,31 @@ def main():
     return 0
 
 
+PROFILE = os.path.join(ROOT, "profiles", "step_tma_kernel_cylinder_128x128x256_f32.md")
+
+
 def lbw_kernel_hash():
     import hashlib
     p = os.path.join(ROOT, "paper_1705_01801_gb300", "csrc", "lbw_step.cu")
     with open(p, "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None when
+    the kernel source changed since the counters were taken."""
+    try:
+        fields = {}
+        with open(PROFILE) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith(("#", "|", " ")):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("step_source_sha256_16") != lbw_kernel_hash():
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 if __name__ == "__main__":
