@@ -102,8 +102,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+WORKLOAD = "cylinder"
+PREC_OVERRIDE = None
+
+
 def workload():
-    wl = W.workload("cylinder")
+    """The benchmark workload (cylinder by default; --workload / --prec select another)."""
+    wl = W.workload(WORKLOAD)
+    if PREC_OVERRIDE is not None:
+        wl.spec = wl.spec.with_(prec=PREC_OVERRIDE)
     return wl
 
 
@@ -179,7 +186,15 @@ def main():
     ap.add_argument("--lbm-steps", type=int, default=LBM_STEPS,
                     help="time steps per benchmark step (default: the workload's 20000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "disk", "trumpet", "torus"])
+    ap.add_argument("--prec", default=None, choices=["f64", "f32", "f16s", "bf16s"],
+                    help="storage override (default: the workload's own)")
     args = ap.parse_args()
+    global WORKLOAD, PREC_OVERRIDE
+    WORKLOAD = args.workload
+    if args.prec:
+        PREC_OVERRIDE = {"f64": W.PREC_F64, "f32": W.PREC_F32, "f16s": W.PREC_F16S,
+                         "bf16s": W.PREC_BF16S}[args.prec]
     if args.impl == "reference":
         return run_reference(args)
 
@@ -193,7 +208,7 @@ def main():
 
     wl = workload()
     spec = wl.spec
-    lbm_steps = args.lbm_steps
+    lbm_steps = args.lbm_steps if args.lbm_steps != LBM_STEPS else wl.steps
     stream = torch.cuda.Stream()
     sh = lbw.ctypes.c_void_p(stream.cuda_stream)
     grid = lbw.Grid(spec, stream=sh)
@@ -244,11 +259,12 @@ def main():
     value = units / (my_ms / 1e3) / 1e6
 
     # ---- roofline of the fused step kernel (algorithmic bytes: 7 loads + 7 stores)
-    bytes_per_node = 14 * 4
+    elem = {W.PREC_F64: 8, W.PREC_F32: 4, W.PREC_F16S: 2, W.PREC_BF16S: 2}[spec.prec]
+    bytes_per_node = 14 * elem
     kernel_ms = sum(step_ms) / (args.steps * lbm_steps)
     achieved = spec.nodes * bytes_per_node / (kernel_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = profiled_traffic()
+    traffic = profiled_traffic() if (WORKLOAD == "cylinder" and PREC_OVERRIDE is None) else None
 
     # ---- end to end through the C ABI with host buffers
     host_pulses = np.ascontiguousarray(wl.pulses)
@@ -298,17 +314,20 @@ def main():
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": my_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"cylinder (r, theta, z) {spec.n[0]}x{spec.n[1]}x{spec.n[2]}, "
-                               f"FP32 storage, {lbm_steps} time steps + spectrum per step, "
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {W.PREC_F64: "f64", W.PREC_F32: "f32", W.PREC_F16S: "f16 storage / f32 math",
+                  W.PREC_BF16S: "bf16 storage / f32 math"}[spec.prec], "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD} {spec.n[0]}x{spec.n[1]}x{spec.n[2]}, "
+                               f"{lbm_steps} time steps + spectrum per step, "
                                f"{nprobe} probes, 8 random-phase Gaussian pulses",
                    "nodes": spec.nodes, "time_steps_per_step": lbm_steps, "c": spec.c,
                    "r_in": spec.x0[0],
-                   "l2": "working set 470 MB > 129 MB L2 (no flush needed)",
+                   "l2": f"working set {2 * 7 * spec.nodes * elem / 1e6:.0f} MB vs 129 MB L2 "
+                         "(no flush between steps)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "step_tma_kernel<float, 7>", "peak_source": peak_kind,
+                     "kernel": "fused step kernel", "peak_source": peak_kind,
                      "bytes_per_node": bytes_per_node, "kernel_us": kernel_ms * 1e3},
         "cpu_baseline": base,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
