@@ -167,6 +167,55 @@ lbw_status lbw_step_count(lbw_grid* g, int64_t* out);
 /* Frees the grid's device memory (stream-ordered) and graphs; NULL is allowed. */
 void lbw_destroy(lbw_grid* g);
 
+/* ------------------------------------------------------------------------------------------
+ * Ensembles: many independent lattices of uneven sizes (each a full instance of the scheme
+ * above with its own geometry and probes) advanced together.  One time step of the whole
+ * ensemble is one launch of a persistent kernel over a (member, tile, q3 segment) work list;
+ * steps are captured in CUDA graphs.  A member's results are bit-identical to a single lattice
+ * run by the register-pipelined step kernel.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct lbw_batch lbw_batch; /* opaque, library-owned */
+
+/* n members (1..65536), all with the same prec; each descriptor is validated as in
+ * lbw_create_grid.  Populations start at zero. */
+lbw_status lbw_batch_create(const lbw_grid_desc* descs, int32_t n, void* stream, lbw_batch** out);
+
+/* Initial state at rest for every member: host_counts[m] pulses for member m, taken in order
+ * from host_pulses (the members' pulse lists concatenated). */
+lbw_status lbw_batch_init(lbw_batch* b, const lbw_pulse* host_pulses, const int32_t* host_counts);
+
+/* per_member probes for every member: host_q = n x per_member x (q1, q2, q3); capacity
+ * samples each.  Resets the series. */
+lbw_status lbw_batch_probe(lbw_batch* b, const int32_t* host_q, int32_t per_member, int64_t capacity);
+
+/* Advance every member by n_steps (asynchronous on the ensemble's stream). */
+lbw_status lbw_batch_step(lbw_batch* b, int64_t n_steps);
+
+/* All series: host_out = n x per_member x capacity doubles; *n_steps = samples recorded. */
+lbw_status lbw_batch_probe_read(lbw_batch* b, double* host_out, int64_t* n_steps);
+
+/* Per member, the spectrum of the sum of its probes (the estimator of lbw_spectrum):
+ * host_freq / host_amp = n x k, host_n_found = n. */
+lbw_status lbw_batch_spectrum(lbw_batch* b, int32_t k, double* host_freq, double* host_amp,
+                              int32_t* host_n_found);
+
+/* Member's populations as doubles (7 x N of that member). */
+lbw_status lbw_batch_get_populations(lbw_batch* b, int32_t member, double* host_f);
+
+/* Autotuner: times candidate launch shapes (rows per tile 4/8/16, planes per q3 segment
+ * 16/32/64, CTAs per SM 1/2/4) for trial_steps steps each and keeps the fastest.  With a
+ * cache_path (JSON lines), a shape stored for the same ensemble signature is reused without
+ * timing and a new choice is appended.  The trial steps run on the ensemble's buffers: call
+ * it before lbw_batch_init.  A text report of the timings goes to report (may be NULL). */
+lbw_status lbw_batch_tune(lbw_batch* b, int32_t trial_steps, const char* cache_path, char* report,
+                          int32_t report_cap);
+
+/* Total nodes and the launch shape in use (any pointer may be NULL). */
+lbw_status lbw_batch_info(lbw_batch* b, int64_t* total_nodes, int32_t* tile_rows, int32_t* seg_planes,
+                          int32_t* ctas_per_sm);
+
+void lbw_batch_destroy(lbw_batch* b);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* lbw_last_error(void);
 

@@ -191,3 +191,45 @@ def workload(name: str) -> Workload:
         return Workload("torus", s, 50000, pulses(s, 4, 1), probes(s, 4, 64),
                         "torus 192x1024x256, R/a = 3")
     raise KeyError(name)
+
+
+def ensemble_member(n_r: int, n_theta: int, n_z: int, a0: float, b: float, alpha: float,
+                    c: float = WAVE_SPEED, prec: int = PREC_F32) -> GridSpec:
+    """One exponential-flare trumpet of the ensemble: rigid walls and rigid ends (halfway
+    bounce-back, D = 1) for clean normal modes."""
+    r_in = r_inner(c, n_theta)
+    return GridSpec(kind=KIND_TRUMPET, n=(n_r, n_theta, n_z),
+                    h=(1.0, 2 * math.pi / n_theta, 1.0), x0=(r_in, 0.0, 0.0), c=c,
+                    geom=(a0, b, alpha, 0.0), profile=PROFILE_EXP,
+                    bc=(BC_BOUNCE, BC_BOUNCE, BC_PERIODIC, BC_PERIODIC, BC_BOUNCE, BC_BOUNCE),
+                    prec=prec)
+
+
+def ensemble(n: int, seed: int = 5, r_range=(32, 96), theta_range=(32, 96), z_range=(128, 512),
+             prec: int = PREC_F32):
+    """n seeded trumpets of uneven sizes (uniform integer sizes in the given ranges) and
+    seeded flares.  Returns (specs, params) with params[m] = (n_r, n_theta, n_z, a0, b, alpha)."""
+    rng = np.random.default_rng(seed)
+    specs, params = [], []
+    for _ in range(n):
+        n_r = int(rng.integers(r_range[0], r_range[1] + 1))
+        n_t = int(rng.integers(theta_range[0], theta_range[1] + 1))
+        n_z = int(rng.integers(z_range[0], z_range[1] + 1))
+        a0, b, alpha = trumpet_params(int(rng.integers(1 << 30)), n_r, n_z)
+        specs.append(ensemble_member(n_r, n_t, n_z, a0, b, alpha, prec=prec))
+        params.append((n_r, n_t, n_z, a0, b, alpha))
+    return specs, params
+
+
+def ensemble_excitation(spec: GridSpec, sigma: float = 3.0):
+    """Pulse and probes at fixed relative positions of a member, so its spectrum depends on
+    its geometry only: one pulse at (r, theta, z) = (0.6 R, 0, 0.3 L) and 8 probes."""
+    n1, n2, n3 = spec.n
+    q = (int(0.6 * n1), 0, int(0.3 * n3))
+    X = embedding(spec, *node_coords(spec, *q))
+    pulse = np.array([[X[0], X[1], X[2], sigma, 1.0]])
+    rel = [(0.3, 0.0, 0.1), (0.5, 0.25, 0.5), (0.7, 0.5, 0.9), (0.9, 0.75, 0.2),
+           (0.4, 0.1, 0.7), (0.8, 0.6, 0.4), (0.2, 0.9, 0.6), (0.65, 0.35, 0.8)]
+    pr = np.array([[min(n1 - 1, int(a * n1)), min(n2 - 1, int(t * n2)), min(n3 - 1, int(z * n3))]
+                   for a, t, z in rel], dtype=np.int32)
+    return pulse, pr

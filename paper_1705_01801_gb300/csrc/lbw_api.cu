@@ -205,6 +205,13 @@ lbw_status build_table(const lbw_grid_desc& d, std::vector<double>& tab) {
   return LBW_OK;
 }
 
+}  // namespace
+
+lbw_status validate_desc(lbw_grid_desc& d) { return validate(d); }
+lbw_status build_force_table(const lbw_grid_desc& d, std::vector<double>& tab) { return build_table(d, tab); }
+
+namespace {
+
 size_t elem_size(int prec) { return prec == LBW_F64 ? 8 : prec == LBW_F32 ? 4 : 2; }
 size_t real_size(int prec) { return prec == LBW_F64 ? 8 : 4; }
 

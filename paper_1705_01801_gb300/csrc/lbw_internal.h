@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "lbw.h"
 
@@ -67,6 +68,10 @@ lbw_status cuda_fail(cudaError_t e, const char* what);
     cudaError_t e_ = (call);                                \
     if (e_ != cudaSuccess) return ::lbw::cuda_fail(e_, #call); \
   } while (0)
+
+// descriptor validation (fills default angular spacings) and the FP64 force-coefficient table
+lbw_status validate_desc(lbw_grid_desc& d);
+lbw_status build_force_table(const lbw_grid_desc& d, std::vector<double>& tab);
 
 // kernels (lbw_step.cu) ---------------------------------------------------------------------
 cudaError_t launch_step(Grid* g, int src);             // one time step, buffer src -> 1-src

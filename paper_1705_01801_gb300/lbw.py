@@ -21,7 +21,10 @@ STATUS_NAMES = ["LBW_OK", "LBW_EINVAL", "LBW_ENOMEM", "LBW_ECUDA", "LBW_EUNSTABL
 # every symbol the header declares (checked by tests/test_abi.py)
 EXPORTS = ["lbw_create_grid", "lbw_init", "lbw_step", "lbw_probe", "lbw_probe_read",
            "lbw_spectrum", "lbw_spectrum_series", "lbw_spectrum_series_static", "lbw_get_field", "lbw_get_populations",
-           "lbw_set_populations", "lbw_step_count", "lbw_destroy", "lbw_last_error"]
+           "lbw_set_populations", "lbw_step_count", "lbw_destroy", "lbw_last_error",
+           "lbw_batch_create", "lbw_batch_init", "lbw_batch_probe", "lbw_batch_step",
+           "lbw_batch_probe_read", "lbw_batch_spectrum", "lbw_batch_get_populations",
+           "lbw_batch_tune", "lbw_batch_info", "lbw_batch_destroy"]
 
 
 class lbw_grid_desc(ctypes.Structure):
@@ -71,6 +74,16 @@ def lib():
                 "lbw_step_count": (st, [vp, ctypes.POINTER(i64)]),
                 "lbw_destroy": (None, [vp]),
                 "lbw_last_error": (ctypes.c_char_p, []),
+                "lbw_batch_create": (st, [ctypes.POINTER(lbw_grid_desc), i32, vp, ctypes.POINTER(vp)]),
+                "lbw_batch_init": (st, [vp, ctypes.POINTER(lbw_pulse), ip]),
+                "lbw_batch_probe": (st, [vp, ip, i32, i64]),
+                "lbw_batch_step": (st, [vp, i64]),
+                "lbw_batch_probe_read": (st, [vp, dp, ctypes.POINTER(i64)]),
+                "lbw_batch_spectrum": (st, [vp, i32, dp, dp, ip]),
+                "lbw_batch_get_populations": (st, [vp, i32, dp]),
+                "lbw_batch_tune": (st, [vp, i32, ctypes.c_char_p, ctypes.c_char_p, i32]),
+                "lbw_batch_info": (st, [vp, ctypes.POINTER(i64), ip, ip, ip]),
+                "lbw_batch_destroy": (None, [vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -271,3 +284,78 @@ class Grid:
 
     def step_count(self):
         return lbw_step_count(self._h)
+
+
+class Batch:
+    """Owner of one lbw_batch: a list of ``lbw_workloads.GridSpec`` in, numpy out."""
+
+    def __init__(self, specs, stream=None):
+        self.specs = list(specs)
+        n = len(self.specs)
+        descs = (lbw_grid_desc * n)(*[make_desc(s) for s in self.specs])
+        out = ctypes.c_void_p()
+        _check(lib().lbw_batch_create(descs, n, stream, ctypes.byref(out)))
+        self._h = out
+        self.n = n
+        self._per = 0
+        self._cap = 0
+
+    def close(self):
+        if self._h:
+            lib().lbw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, trial_steps=3, cache_path=None):
+        rep = ctypes.create_string_buffer(8192)
+        _check(lib().lbw_batch_tune(self._h, int(trial_steps),
+                                    cache_path.encode() if cache_path else None, rep, 8192))
+        return rep.value.decode()
+
+    def info(self):
+        t, by, lz, cps = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().lbw_batch_info(self._h, ctypes.byref(t), ctypes.byref(by), ctypes.byref(lz),
+                                    ctypes.byref(cps)))
+        return {"nodes": t.value, "tile_rows": by.value, "seg_planes": lz.value,
+                "ctas_per_sm": cps.value}
+
+    def init(self, pulses_per_member):
+        counts = np.array([len(np.asarray(p).reshape(-1, 5)) for p in pulses_per_member], np.int32)
+        allp = np.concatenate([np.asarray(p, np.float64).reshape(-1, 5) for p in pulses_per_member])
+        arr = (lbw_pulse * max(1, len(allp)))()
+        for k, row in enumerate(allp):
+            arr[k].x[0], arr[k].x[1], arr[k].x[2], arr[k].sigma, arr[k].amp = row
+        _check(lib().lbw_batch_init(self._h, arr, _ip(counts)))
+
+    def set_probes(self, q, cap):
+        q = np.ascontiguousarray(np.asarray(q, np.int32).reshape(self.n, -1, 3))
+        _check(lib().lbw_batch_probe(self._h, _ip(q), q.shape[1], int(cap)))
+        self._per, self._cap = q.shape[1], int(cap)
+
+    def step(self, n):
+        _check(lib().lbw_batch_step(self._h, int(n)))
+
+    def read_probes(self):
+        out = np.zeros((self.n, max(1, self._per), max(1, self._cap)))
+        n = ctypes.c_int64()
+        _check(lib().lbw_batch_probe_read(self._h, _dp(out), ctypes.byref(n)))
+        return out[:, : self._per, : n.value]
+
+    def spectrum(self, k=8):
+        f = np.zeros((self.n, k))
+        a = np.zeros((self.n, k))
+        c = np.zeros(self.n, np.int32)
+        _check(lib().lbw_batch_spectrum(self._h, int(k), _dp(f), _dp(a), _ip(c)))
+        return f, a, c
+
+    def get_f(self, member):
+        s = self.specs[member]
+        nn = int(np.prod(s.n))
+        out = np.zeros(7 * nn)
+        _check(lib().lbw_batch_get_populations(self._h, int(member), _dp(out)))
+        return out.reshape(7, s.n[2], s.n[0], s.n[1])
