@@ -151,16 +151,6 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
         "r"(bar) : "memory");
 }
 
-// Pull of one node from global memory with the face rules (rarely taken paths).
-template <typename S>
-__device__ __noinline__ void pull_global(const StepArgs<S>& a, int q1, int q2, int q3,
-                                         typename Store<S>::R* f) {
-  typename Store<S>::R g[7];
-  pull(a, q1, q2, q3, g);
-#pragma unroll
-  for (int i = 0; i < 7; ++i) f[i] = g[i];
-}
-
 template <int BY>
 struct TmaLayout {
   // per population: main box (BY+2) x BX, left / right halo boxes (BY+2) x V, 128-B aligned
@@ -278,13 +268,16 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       if (xr >= a.n2) xr -= a.n2;
       const unsigned tx_pop = (unsigned)(ROWS * BX * ES) + (hl ? ROWS * 16u : 0u) + (hr ? ROWS * 16u : 0u);
       int s = 0, use = 0;
-      int issued = z0 - 2;
-      for (int p = z0 - 1; p <= z1 + 1; ++p) {
+      int issued = z0 - 3;
+      for (int p = z0 - 2; p <= z1 + 1; ++p) {
         if (use > 0 && !wait_bar(&empty[s], (unsigned)((use - 1) & 1))) break;
         const unsigned bar = smem_u32(&full[s]);
         const int pg = resolve(p, a.n3, p3);
         if (pg < 0) {
           mbar_expect_tx(bar, 0);
+        } else if (p == z0 - 2) {  // only population 5 of this plane streams into the segment
+          mbar_expect_tx(bar, (unsigned)(ROWS * BX * ES));
+          tma_load_4d(smem_u32(slots + s * SLOTB + 5 * POPB), &tm_main, x0, y0 - 1, pg, 5, bar);
         } else {
           const bool tab = p >= z0 && p < z1;
           mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
@@ -302,8 +295,8 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
         if (++s == NB) { s = 0; ++use; }
       }
       // drain: the last NB staged planes have landed before the CTA exits (bounded)
-      for (int p = max(z0 - 1, issued - NB + 1); p <= issued; ++p) {
-        const int k = p - (z0 - 1);
+      for (int p = max(z0 - 2, issued - NB + 1); p <= issued; ++p) {
+        const int k = p - (z0 - 2);
         wait_bar(&full[k % NB], (unsigned)((k / NB) & 1));
       }
     }
@@ -321,19 +314,18 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     // pops 1 / 2 at the pull or at the q1-face rule
     const int own = w * BX * ES + c0 * ES;
     int o1 = POPB + own, o2 = 2 * POPB + own;
+    // the face rules of rows 0 and n1 - 1 read the staged rows next to the node: the launch
+    // shape keeps halo rows off the faces (y0 - 1 > 0 or < 0, y0 + BY != n1 - 1)
     R m1 = sc1, m2 = sc1;
-    bool slow = false;
     if (r1 == 0) {
       const int b = a.bc[0];
       if (b == LBW_BC_FREE) o1 = POPB + own + BX * ES;
       else { o1 = 2 * POPB + own - BX * ES; m1 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
-      if (!interior) slow = true;
     }
     if (r1 == a.n1 - 1) {
       const int b = a.bc[1];
       if (b == LBW_BC_FREE) o2 = 2 * POPB + own - BX * ES;
       else { o2 = POPB + own + BX * ES; m2 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
-      if (!interior) slow = true;
     }
     // pop 3 of node c0 reads column c0 - 1 (left halo box for lane 0), pop 4 of node c0 + 1
     // reads column c0 + 2 (right halo box for lane 31)
@@ -346,7 +338,6 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     const int hr1 = resolve(hq1, a.n1, false), hr2 = resolve(hq2, a.n2, p2);
     int h0 = 0, h1 = 0, h2 = 0, h3 = 0, h4 = 0, h56 = 0;  // byte offsets in a slot
     R hm1 = sc1, hm2 = sc1;
-    bool hslow = false;
     if (hcol) {
       const int hw = lane + 1;
       // column -1 lives in the left halo box (index V - 1), column BX in the right one (0)
@@ -369,7 +360,8 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
         if (b == LBW_BC_FREE) h2 = hat(2, hw - 1);
         else { h2 = hat(1, hw + 1); hm2 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
       }
-      hslow = !p2 && hr2 >= 0 && (hr2 == 0 || hr2 == a.n2 - 1);
+      // a halo column is never on a q2 face (the q2 extent is a multiple of BX), so its own
+      // q2 pulls are plain
     }
     const int hrho = (lane + 1) * PW + ((w == 0) ? 1 : BX + 2);
 
@@ -377,8 +369,8 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     const long long n12 = (long long)a.n1 * a.n2;
     S* const dst_z0 = a.fout + node(owner ? q1 : 0, q2, z0, a.n1, a.n2);
 
-    // step A of pulled plane u: populations into f, rho into rr and the rho plane
-#define LBW_STEP_A(u, f, rr, slm, sl0, slp, rbu)                                                  \
+    // step A of pulled plane u: populations into f, rho into rr and (wr) the rho plane
+#define LBW_STEP_A(u, f, rr, slm, sl0, slp, rbu, wr)                                              \
     do {                                                                                          \
       const int r3_ = resolve((u), a.n3, p3);                                                     \
       const unsigned char* S0 = slots + (sl0) * SLOTB;                                            \
@@ -399,14 +391,6 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       }                                                                                           \
       if (r3_ < 0 || r1 < 0) {                                                                    \
         rr[0] = R(0); rr[1] = R(0);                                                               \
-      } else if (slow) {                                                                          \
-        _Pragma("unroll 1") for (int k_ = 0; k_ < NPT; ++k_) {                                  \
-          R g_[7];                                                                                \
-          pull_global(a, r1, q2 + k_, r3_, g_);                                                   \
-          const R s_ = ((g_[0] + g_[1]) + (g_[2] + g_[3])) + ((g_[4] + g_[5]) + g_[6]);           \
-          if (k_ == 0) { for (int i_ = 0; i_ < 7; ++i_) f[i_][0] = g_[i_]; rr[0] = s_; }          \
-          else { for (int i_ = 0; i_ < 7; ++i_) f[i_][1] = g_[i_]; rr[1] = s_; }                  \
-        }                                                                                         \
       } else {                                                                                    \
         R t3_[NPT], t4_[NPT];                                                                     \
         Vec<S>::ld(reinterpret_cast<const S*>(S0 + own), f[0]);                                   \
@@ -434,15 +418,13 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
         _Pragma("unroll") for (int k_ = 0; k_ < NPT; ++k_)                                      \
           rr[k_] = ((f[0][k_] + f[1][k_]) + (f[2][k_] + f[3][k_])) + ((f[4][k_] + f[5][k_]) + f[6][k_]); \
       }                                                                                           \
-      R* out_ = rho_s + (rbu) * PS;                                                               \
-      RVec<R>::st(out_ + w * PW + 2 + c0, rr);                                                    \
-      if (hcol) {                                                                                 \
-        R h_ = R(0);                                                                              \
-        if (r3_ >= 0 && hr1 >= 0 && hr2 >= 0) {                                                   \
-          R g_[7];                                                                                \
-          if (hslow) {                                                                            \
-            pull_global(a, hr1, hr2, r3_, g_);                                                    \
-          } else {                                                                                \
+      if (wr) {                                                                                   \
+        R* out_ = rho_s + (rbu) * PS;                                                             \
+        RVec<R>::st(out_ + w * PW + 2 + c0, rr);                                                  \
+        if (hcol) {                                                                               \
+          R h_ = R(0);                                                                            \
+          if (r3_ >= 0 && hr1 >= 0 && hr2 >= 0) {                                                 \
+            R g_[7];                                                                              \
             g_[0] = sc0 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h0));                 \
             g_[1] = hm1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h1));                 \
             g_[2] = hm2 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h2));                 \
@@ -450,10 +432,10 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
             g_[4] = sc1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h4));                 \
             g_[5] = m5_ * Store<S>::ld_smem(reinterpret_cast<const S*>(B5 + h56));                \
             g_[6] = m6_ * Store<S>::ld_smem(reinterpret_cast<const S*>(B6 + h56));                \
+            h_ = ((g_[0] + g_[1]) + (g_[2] + g_[3])) + ((g_[4] + g_[5]) + g_[6]);                 \
           }                                                                                       \
-          h_ = ((g_[0] + g_[1]) + (g_[2] + g_[3])) + ((g_[4] + g_[5]) + g_[6]);                   \
+          out_[hrho] = h_;                                                                        \
         }                                                                                         \
-        out_[hrho] = h_;                                                                          \
       }                                                                                           \
     } while (0)
 
@@ -514,29 +496,23 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       }                                                                                           \
     } while (0)
 
-    // rho of plane z0 - 1 (own column; its pop 5 lies in the unstaged plane z0 - 2)
-    {
-      const int r3 = resolve(z0 - 1, a.n3, p3);
-      for (int k = 0; k < NPT; ++k) {
-        R v = R(0);
-        if (owner && r3 >= 0) {
-          R g[7];
-          pull_global(a, r1, q2 + k, r3, g);
-          v = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
-        }
-        if (k == 0) rA[0] = v; else rA[1] = v;
-      }
-    }
+    // rho of plane z0 - 1 at the own nodes, from the staged planes z0 - 2 (population 5 only),
+    // z0 - 1 and z0; then step A of plane z0
     bool ok = wait_bar(&full[0], 0) && wait_bar(&full[1], 0) && wait_bar(&full[2], 0);
-    if (ok) LBW_STEP_A(z0, fA, rB, 0, 1, 2, 0);
-    if (lane == 0) mbar_arrive(smem_u32(&empty[0]));  // raw plane z0 - 1 is no longer needed
+    if (ok && owner) LBW_STEP_A(z0 - 1, fB, rA, 0, 1, 2, 2, false);
+    if (lane == 0) mbar_arrive(smem_u32(&empty[0]));  // plane z0 - 2 is no longer needed
+    ok = ok && wait_bar(&full[3], 0);
+    if (ok) LBW_STEP_A(z0, fA, rB, 1, 2, 3, 0, true);
+    if (lane == 0) mbar_arrive(smem_u32(&empty[1]));  // nor is plane z0 - 1
     named_sync(1, NCW * 32);
+    if (abort_flag) ok = false;
     int z = z0;
-    // slots of raw planes z, z + 1, z + 2 (plane z0 - 1 sits in slot 0) and the fill count of
+    // slots of raw planes z, z + 1, z + 2 (plane z0 - 2 sits in slot 0) and the fill count of
     // plane z + 2's slot, advanced plane by plane
     // rho planes rotate through three buffers: a warp writing plane z + 1's buffer has passed
-    // the barrier that follows every read of that buffer (plane z - 2)
-    int sz = 1, s1 = 2, s2 = 3, u2 = 0, rbz = 0, rb1 = 1;
+    // the barrier that follows every read of that buffer (plane z - 2); the rows of plane
+    // z0 - 1 written into buffer 2 above are never read
+    int sz = 2, s1 = 3, s2 = 4, u2 = 0, rbz = 0, rb1 = 1;
 #define LBW_ADVANCE()                                                                             \
     do {                                                                                          \
       rbz = rb1;                                                                                  \
@@ -550,7 +526,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
 #define LBW_ITER(zz, fc, fn, rp, rc, rn)                                                          \
     do {                                                                                          \
       if (!abort_flag && !wait_bar(&full[s2], (unsigned)(u2 & 1))) ok = false;                    \
-      if (ok && !abort_flag) LBW_STEP_A((zz) + 1, fn, rn, sz, s1, s2, rb1);                       \
+      if (ok && !abort_flag) LBW_STEP_A((zz) + 1, fn, rn, sz, s1, s2, rb1, true);                 \
       named_sync(1, NCW * 32);                                                                    \
       if (abort_flag) ok = false;                                                                 \
       if (ok && owner) LBW_STEP_B((zz), fc, rp, rc, rn, sz, rbz);                                 \
@@ -959,6 +935,7 @@ void step_launch_shape(Grid* g) {
     for (int c = 0; c < 2; ++c) {
       const int by = bys[c], threads = 32 * (by + 3);
       if ((long long)smem[c] > smem_max || regs[c] > 255) continue;
+      if ((n1 - 1) % by == 0) continue;  // a halo row would sit on the q1 = n1 - 1 face
       const int rr = (regs[c] + 7) & ~7;
       int per_sm = std::min<int>(2048 / threads, (int)((228LL * 1024) / (smem[c] + 1024)));
       per_sm = std::max(1, std::min(per_sm, 65536 / (rr * threads)));
