@@ -216,6 +216,40 @@ lbw_status lbw_batch_info(lbw_batch* b, int64_t* total_nodes, int32_t* tile_rows
 
 void lbw_batch_destroy(lbw_batch* b);
 
+/* ------------------------------------------------------------------------------------------
+ * Surrogate: a multilayer perceptron from ensemble geometry parameters to mode frequencies,
+ * trained and evaluated on the device (the paper has no counterpart; the lattice-Boltzmann
+ * runs stay the judge of its error).  depth weight layers in -> hidden -> ... -> out, tanh
+ * after every layer but the last.  Loss: mean over samples and outputs of (y - t)^2.
+ * Parameters: one FP32 vector, per layer W (out x in, row-major) then b (out).  Host arrays
+ * are row-major float32 (n x in inputs, n x out targets).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct lbw_mlp lbw_mlp; /* opaque, library-owned */
+
+/* Glorot-uniform weights from a counter-based generator seeded by `seed`, zero biases. */
+lbw_status lbw_mlp_create(int32_t in_dim, int32_t hidden, int32_t depth, int32_t out_dim, uint64_t seed,
+                          void* stream, lbw_mlp** out);
+lbw_status lbw_mlp_param_count(lbw_mlp* q, int64_t* n);
+lbw_status lbw_mlp_get_params(lbw_mlp* q, float* host_params);
+/* Also resets the Adam moments. */
+lbw_status lbw_mlp_set_params(lbw_mlp* q, const float* host_params);
+/* FP32 forward pass of n rows. */
+lbw_status lbw_mlp_forward(lbw_mlp* q, const float* host_x, int32_t n, float* host_y);
+/* Forward pass with the weights rounded to BF16 (biases and accumulation FP32). */
+lbw_status lbw_mlp_predict_bf16(lbw_mlp* q, const float* host_x, int32_t n, float* host_y);
+/* Loss and its gradient with respect to all parameters for one batch of n rows
+ * (host_grad may be NULL). */
+lbw_status lbw_mlp_grad(lbw_mlp* q, const float* host_x, const float* host_t, int32_t n, float* host_grad,
+                        float* host_loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with a caller gradient. */
+lbw_status lbw_mlp_adam_step(lbw_mlp* q, const float* host_grad, float lr);
+/* n_steps Adam steps on minibatches of `batch` rows of the n samples: step s uses rows
+ * host_order[s * batch .. s * batch + batch - 1] (the caller draws the order).  host_loss
+ * (may be NULL) receives the minibatch loss before each step. */
+lbw_status lbw_mlp_train(lbw_mlp* q, const float* host_x, const float* host_t, int32_t n,
+                         const int32_t* host_order, int32_t n_steps, int32_t batch, float lr, float* host_loss);
+void lbw_mlp_destroy(lbw_mlp* q);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* lbw_last_error(void);
 

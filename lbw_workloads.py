@@ -221,15 +221,18 @@ def ensemble(n: int, seed: int = 5, r_range=(32, 96), theta_range=(32, 96), z_ra
     return specs, params
 
 
-def ensemble_excitation(spec: GridSpec, sigma: float = 3.0):
-    """Pulse and probes at fixed relative positions of a member, so its spectrum depends on
-    its geometry only: one pulse at (r, theta, z) = (0.6 R, 0, 0.3 L) and 8 probes."""
+def ensemble_excitation(spec: GridSpec, sigma: float = 3.0, n_ring: int = 12):
+    """Pulses and probes at fixed relative positions of a member, so its spectrum depends on
+    its geometry only.  A ring of n_ring Gaussian pulses next to the rigid outer wall at the
+    q3 = 0 end (nodes (n1 - 2, j n2 / n_ring, 1)) excites axisymmetric modes (azimuthal orders
+    that are multiples of n_ring aside); 8 probes on a ring at the opposite corner
+    (n1 - 1, j n2 / 8, n3 - 1) record them.  With rigid walls and ends every axisymmetric mode
+    has an antinode at both corners, so the summed probes see each mode without the
+    cancellations that scattered probes suffer."""
     n1, n2, n3 = spec.n
-    q = (int(0.6 * n1), 0, int(0.3 * n3))
-    X = embedding(spec, *node_coords(spec, *q))
-    pulse = np.array([[X[0], X[1], X[2], sigma, 1.0]])
-    rel = [(0.3, 0.0, 0.1), (0.5, 0.25, 0.5), (0.7, 0.5, 0.9), (0.9, 0.75, 0.2),
-           (0.4, 0.1, 0.7), (0.8, 0.6, 0.4), (0.2, 0.9, 0.6), (0.65, 0.35, 0.8)]
-    pr = np.array([[min(n1 - 1, int(a * n1)), min(n2 - 1, int(t * n2)), min(n3 - 1, int(z * n3))]
-                   for a, t, z in rel], dtype=np.int32)
-    return pulse, pr
+    pulse = []
+    for j in range(n_ring):
+        X = embedding(spec, *node_coords(spec, n1 - 2, j * n2 / n_ring, 1))
+        pulse.append([X[0], X[1], X[2], sigma, 1.0])
+    pr = np.array([[n1 - 1, (j * n2) // 8, n3 - 1] for j in range(8)], dtype=np.int32)
+    return np.array(pulse), pr

@@ -24,7 +24,10 @@ EXPORTS = ["lbw_create_grid", "lbw_init", "lbw_step", "lbw_probe", "lbw_probe_re
            "lbw_set_populations", "lbw_step_count", "lbw_destroy", "lbw_last_error",
            "lbw_batch_create", "lbw_batch_init", "lbw_batch_probe", "lbw_batch_step",
            "lbw_batch_probe_read", "lbw_batch_spectrum", "lbw_batch_get_populations",
-           "lbw_batch_tune", "lbw_batch_info", "lbw_batch_destroy"]
+           "lbw_batch_tune", "lbw_batch_info", "lbw_batch_destroy",
+           "lbw_mlp_create", "lbw_mlp_param_count", "lbw_mlp_get_params", "lbw_mlp_set_params",
+           "lbw_mlp_forward", "lbw_mlp_predict_bf16", "lbw_mlp_grad", "lbw_mlp_adam_step",
+           "lbw_mlp_train", "lbw_mlp_destroy"]
 
 
 class lbw_grid_desc(ctypes.Structure):
@@ -58,6 +61,7 @@ def lib():
             L = ctypes.CDLL(_build.build())
             vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
             ip = ctypes.POINTER(ctypes.c_int32)
+            fp = ctypes.POINTER(ctypes.c_float)
             st = ctypes.c_int
             sig = {
                 "lbw_create_grid": (st, [ctypes.POINTER(lbw_grid_desc), vp, ctypes.POINTER(vp)]),
@@ -84,6 +88,16 @@ def lib():
                 "lbw_batch_tune": (st, [vp, i32, ctypes.c_char_p, ctypes.c_char_p, i32]),
                 "lbw_batch_info": (st, [vp, ctypes.POINTER(i64), ip, ip, ip]),
                 "lbw_batch_destroy": (None, [vp]),
+                "lbw_mlp_create": (st, [i32, i32, i32, i32, ctypes.c_uint64, vp, ctypes.POINTER(vp)]),
+                "lbw_mlp_param_count": (st, [vp, ctypes.POINTER(i64)]),
+                "lbw_mlp_get_params": (st, [vp, fp]),
+                "lbw_mlp_set_params": (st, [vp, fp]),
+                "lbw_mlp_forward": (st, [vp, fp, i32, fp]),
+                "lbw_mlp_predict_bf16": (st, [vp, fp, i32, fp]),
+                "lbw_mlp_grad": (st, [vp, fp, fp, i32, fp, fp]),
+                "lbw_mlp_adam_step": (st, [vp, fp, ctypes.c_float]),
+                "lbw_mlp_train": (st, [vp, fp, fp, i32, ip, i32, i32, ctypes.c_float, fp]),
+                "lbw_mlp_destroy": (None, [vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -359,3 +373,76 @@ class Batch:
         out = np.zeros(7 * nn)
         _check(lib().lbw_batch_get_populations(self._h, int(member), _dp(out)))
         return out.reshape(7, s.n[2], s.n[0], s.n[1])
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class MLP:
+    """Owner of one lbw_mlp (numpy float32 in / out)."""
+
+    def __init__(self, in_dim, hidden=256, depth=4, out_dim=8, seed=0, stream=None):
+        out = ctypes.c_void_p()
+        _check(lib().lbw_mlp_create(int(in_dim), int(hidden), int(depth), int(out_dim),
+                                    ctypes.c_uint64(seed), stream, ctypes.byref(out)))
+        self._h = out
+        self.in_dim, self.out_dim = int(in_dim), int(out_dim)
+        n = ctypes.c_int64()
+        _check(lib().lbw_mlp_param_count(self._h, ctypes.byref(n)))
+        self.nparam = n.value
+
+    def close(self):
+        if self._h:
+            lib().lbw_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        p = np.zeros(self.nparam, np.float32)
+        _check(lib().lbw_mlp_get_params(self._h, _fp(p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, np.float32))
+        assert p.size == self.nparam
+        _check(lib().lbw_mlp_set_params(self._h, _fp(p)))
+
+    def forward(self, x):
+        x = np.ascontiguousarray(np.asarray(x, np.float32))
+        y = np.zeros((x.shape[0], self.out_dim), np.float32)
+        _check(lib().lbw_mlp_forward(self._h, _fp(x), x.shape[0], _fp(y)))
+        return y
+
+    def predict_bf16(self, x):
+        x = np.ascontiguousarray(np.asarray(x, np.float32))
+        y = np.zeros((x.shape[0], self.out_dim), np.float32)
+        _check(lib().lbw_mlp_predict_bf16(self._h, _fp(x), x.shape[0], _fp(y)))
+        return y
+
+    def grad(self, x, t):
+        x = np.ascontiguousarray(np.asarray(x, np.float32))
+        t = np.ascontiguousarray(np.asarray(t, np.float32))
+        g = np.zeros(self.nparam, np.float32)
+        loss = np.zeros(1, np.float32)
+        _check(lib().lbw_mlp_grad(self._h, _fp(x), _fp(t), x.shape[0], _fp(g), _fp(loss)))
+        return float(loss[0]), g
+
+    def adam_step(self, g, lr):
+        g = np.ascontiguousarray(np.asarray(g, np.float32))
+        _check(lib().lbw_mlp_adam_step(self._h, _fp(g), ctypes.c_float(lr)))
+
+    def train(self, x, t, order, batch, lr):
+        x = np.ascontiguousarray(np.asarray(x, np.float32))
+        t = np.ascontiguousarray(np.asarray(t, np.float32))
+        order = np.ascontiguousarray(np.asarray(order, np.int32))
+        steps = order.size // batch
+        loss = np.zeros(max(1, steps), np.float32)
+        _check(lib().lbw_mlp_train(self._h, _fp(x), _fp(t), x.shape[0], _ip(order), steps, int(batch),
+                                   ctypes.c_float(lr), _fp(loss)))
+        return loss[:steps]

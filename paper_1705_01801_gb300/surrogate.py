@@ -1,0 +1,95 @@
+"""Surrogate from trumpet geometry to its lowest mode frequencies.
+
+The batched lattice-Boltzmann ensemble (lbw_batch_*) measures, for every member, the spectrum
+of the sum of its probes (a ring of pulses at one rigid corner, a ring of probes at the other,
+so the axisymmetric modes dominate); the lowest `n_modes` frequencies among its strongest
+peaks are the targets.  A multilayer perceptron (lbw_mlp_*: device forward / backward / Adam
+kernels, BF16-weight inference) maps normalised geometry features to those frequencies.  The
+lattice-Boltzmann runs remain the judge: `measure` gives the reference values the surrogate
+is trained on and checked against.  All arithmetic runs in the library's kernels; this module
+only assembles arrays.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+import lbw_workloads as W
+
+from . import lbw
+
+FEATURE_NAMES = ["R_outer / 100", "L / 512", "a(L) / a(0)", "alpha L", "n_theta / 96",
+                 "r_in / R_outer", "b / (a0 + b)"]
+
+
+def features(spec: W.GridSpec) -> np.ndarray:
+    """Normalised geometry of an exponential-flare trumpet member."""
+    n1, n2, n3 = spec.n
+    r_in = spec.x0[0]
+    R = r_in + n1 * spec.h[0]
+    L = n3 * spec.h[2]
+    a0, b, al = spec.geom[:3]
+    ratio = (a0 + b * math.exp(al * L)) / (a0 + b)
+    return np.array([R / 100.0, L / 512.0, ratio, al * L, n2 / 96.0, r_in / R, b / (a0 + b)],
+                    dtype=np.float32)
+
+
+def measure(specs, steps: int, k_strong: int = 24, n_modes: int = 8, rel_amp: float = 0.05,
+            tune: bool = True):
+    """Run the ensemble for `steps` time steps and return (freqs [n, n_modes], valid [n],
+    seconds of device work).  Targets are the lowest n_modes frequencies (rad / step) among the
+    k_strong strongest spectral peaks whose amplitude is at least rel_amp of the strongest
+    (window side lobes stay below it); members with fewer such peaks are marked invalid."""
+    import torch
+    b = lbw.Batch(specs)
+    if tune:
+        b.tune(trial_steps=2)
+    exc = [W.ensemble_excitation(s) for s in specs]
+    b.init([e[0] for e in exc])
+    b.set_probes(np.stack([e[1] for e in exc]), steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    f, a, cnt = b.spectrum(k_strong)
+    seconds = time.perf_counter() - t0
+    out = np.zeros((len(specs), n_modes))
+    valid = np.zeros(len(specs), bool)
+    for m in range(len(specs)):
+        fm, am = f[m, : cnt[m]], a[m, : cnt[m]]
+        if fm.size == 0:
+            continue
+        fm = np.sort(fm[am >= rel_amp * am.max()])
+        if fm.size >= n_modes:
+            out[m] = fm[:n_modes]
+            valid[m] = True
+    b.close()
+    return out, valid, seconds
+
+
+class Surrogate:
+    """Standardised inputs and outputs around an lbw.MLP (4 weight layers, 256 wide)."""
+
+    def __init__(self, in_dim: int = len(FEATURE_NAMES), out_dim: int = 8, hidden: int = 256,
+                 depth: int = 4, seed: int = 0):
+        self.net = lbw.MLP(in_dim, hidden=hidden, depth=depth, out_dim=out_dim, seed=seed)
+        self.mx = self.sx = self.my = self.sy = None
+
+    def fit(self, X, Y, steps: int = 4000, batch: int = 64, lr: float = 1e-3, seed: int = 0):
+        X = np.asarray(X, np.float64)
+        Y = np.log(np.asarray(Y, np.float64))  # frequencies are positive and span decades
+        self.mx, self.sx = X.mean(0), X.std(0) + 1e-12
+        self.my, self.sy = Y.mean(0), Y.std(0) + 1e-12
+        Xn = ((X - self.mx) / self.sx).astype(np.float32)
+        Yn = ((Y - self.my) / self.sy).astype(np.float32)
+        rng = np.random.default_rng(seed)  # minibatch order drawn here, passed to the kernels
+        per_epoch = max(1, len(Xn) // batch)
+        order = np.concatenate([rng.permutation(len(Xn))[: per_epoch * batch]
+                                for _ in range(math.ceil(steps / per_epoch))])[: steps * batch]
+        return self.net.train(Xn, Yn, order, batch, lr)
+
+    def predict(self, X, bf16: bool = True):
+        Xn = ((np.asarray(X, np.float64) - self.mx) / self.sx).astype(np.float32)
+        Yn = self.net.predict_bf16(Xn) if bf16 else self.net.forward(Xn)
+        return np.exp(Yn.astype(np.float64) * self.sy + self.my)

@@ -1,0 +1,90 @@
+"""Device surrogate network (forward, backward, Adam, BF16 inference) against the FP64
+oracle, and the trained surrogate against the lattice-Boltzmann ensemble it learns from."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+
+
+def _net(seed=3, in_dim=7, hidden=64, depth=4, out_dim=8):
+    from paper_1705_01801_gb300 import lbw
+    return lbw.MLP(in_dim, hidden=hidden, depth=depth, out_dim=out_dim, seed=seed)
+
+
+def test_forward_and_gradient_match_oracle():
+    """FP32 device gradients of the mean squared error against FP64 reverse mode: within
+    1e-4 of the largest gradient entry (FP32 sums over at most 256 terms)."""
+    net = _net(hidden=256)
+    rng = np.random.default_rng(0)
+    p = net.get_params().astype(np.float64)
+    dims = M.layer_dims(7, 256, 4, 8)
+    x = rng.normal(size=(96, 7)).astype(np.float32)
+    t = rng.normal(size=(96, 8)).astype(np.float32)
+    y = net.forward(x)
+    yo = M.forward(p, dims, x)[-1]
+    np.testing.assert_allclose(y, yo, rtol=0, atol=1e-5 * np.abs(yo).max())
+    loss, g = net.grad(x, t)
+    lo, go = M.loss_and_grad(p, dims, x, t)
+    assert abs(loss - lo) <= 1e-5 * lo
+    np.testing.assert_allclose(g, go, rtol=0, atol=1e-4 * np.abs(go).max())
+
+
+def test_adam_step_matches_oracle():
+    net = _net()
+    p = net.get_params().astype(np.float64)
+    rng = np.random.default_rng(1)
+    g = rng.normal(size=p.size).astype(np.float32)
+    net.adam_step(g, 1e-3)
+    net.adam_step(0.5 * g, 1e-3)
+    po, m1, m2 = M.adam(p, g.astype(np.float64), np.zeros_like(p), np.zeros_like(p), 1, 1e-3)
+    po, m1, m2 = M.adam(po, 0.5 * g.astype(np.float64), m1, m2, 2, 1e-3)
+    np.testing.assert_allclose(net.get_params(), po, rtol=0, atol=1e-6)
+
+
+def test_bf16_inference_close_to_fp32():
+    net = _net(hidden=256)
+    x = np.random.default_rng(2).normal(size=(64, 7)).astype(np.float32)
+    y, yb = net.forward(x), net.predict_bf16(x)
+    assert np.abs(yb - y).max() <= 3e-2 * np.abs(y).max()
+
+
+def test_training_fits_a_smooth_map():
+    net = _net(hidden=128)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-1, 1, size=(512, 7)).astype(np.float32)
+    t = np.stack([np.sin(x[:, 0] * (k + 1)) + x[:, 1] * x[:, 2] for k in range(8)], 1).astype(np.float32)
+    order = np.concatenate([rng.permutation(512) for _ in range(250)])
+    loss = net.train(x, t, order, 64, 2e-3)
+    assert loss[-50:].mean() < 0.02 * loss[:10].mean()
+
+
+def test_surrogate_against_ensemble_judge():
+    """Train on spectra the batched LBM measures for seeded trumpets and check held-out
+    members: the surrogate answers in microseconds what the ensemble takes seconds for, at a
+    stated mode-frequency error (mean relative, held out)."""
+    import lbw_workloads as W
+    from paper_1705_01801_gb300 import surrogate as S
+    specs, _ = W.ensemble(384, seed=21, r_range=(12, 24), theta_range=(32, 48), z_range=(40, 80))
+    freqs, valid, lbm_s = S.measure(specs, steps=4000, tune=False)
+    X = np.stack([S.features(s) for s in specs])[valid]
+    Y = freqs[valid]
+    ntr = int(0.8 * len(X))
+    sur = S.Surrogate(hidden=256, depth=4, seed=0)
+    sur.fit(X[:ntr], Y[:ntr], steps=4000, batch=32, lr=1e-3)
+    t0 = time.perf_counter()
+    pred = sur.predict(X[ntr:])
+    sur_s = time.perf_counter() - t0
+    err = np.abs(pred - Y[ntr:]) / Y[ntr:]
+    base = np.abs(np.exp(np.log(Y[:ntr]).mean(0)) - Y[ntr:]) / Y[ntr:]  # no-network baseline
+    print(f"valid {valid.mean():.3f}; held-out mean rel error {err.mean():.4f} "
+          f"(per mode {np.round(err.mean(0), 3)}; mean predictor {base.mean():.4f}); "
+          f"ensemble {lbm_s:.2f} s for {len(specs)} members, surrogate {sur_s * 1e3:.2f} ms")
+    speedup = (lbm_s / len(specs)) / (sur_s / (len(X) - ntr))
+    print(f"per-geometry speedup of the surrogate over the ensemble run: {speedup:.0f}x")
+    assert valid.mean() > 0.8
+    assert err.mean() < 0.5 * base.mean() and err.mean() < 0.08
+    assert speedup > 100
