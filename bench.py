@@ -42,6 +42,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over the ranks of the default process group (x itself without one): the
+    whole job takes as long as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes: int, time_steps: int, world_size: int, seconds: float) -> float:
+    """Lattice updates of all ranks (one replica each) per second, in millions."""
+    return nodes * time_steps * world_size / seconds / 1e6
+
+
 def _peaks():
     try:
         with open(PEAKS_FILE) as fh:
@@ -250,13 +267,8 @@ def main():
             tot_ms.append(t)
             step_ms.append(s)
     barrier()
-    my_ms = sum(tot_ms)
-    if ws > 1:
-        tt = torch.tensor([my_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        my_ms = float(tt.item())
-    units = spec.nodes * lbm_steps * args.steps * ws
-    value = units / (my_ms / 1e3) / 1e6
+    my_ms = max_over_ranks(sum(tot_ms), device="cuda")
+    value = whole_job_mlups(spec.nodes, lbm_steps * args.steps, ws, my_ms / 1e3)
 
     # ---- roofline of the fused step kernel (algorithmic bytes: 7 loads + 7 stores)
     elem = {W.PREC_F64: 8, W.PREC_F32: 4, W.PREC_F16S: 2, W.PREC_BF16S: 2}[spec.prec]
@@ -286,12 +298,8 @@ def main():
     for _ in range(args.steps):
         series, _ = e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = units / e2e_s / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")
+    e2e_value = whole_job_mlups(spec.nodes, lbm_steps * args.steps, ws, e2e_s)
     h2d = host_pulses.nbytes + host_probes.nbytes
     d2h = nprobe * lbm_steps * 8 + 8 * 8 * 2
 

@@ -169,8 +169,15 @@ __device__ __forceinline__ void mbar_init_count(unsigned bar, unsigned count) {
 __device__ __forceinline__ void mbar_arrive(unsigned bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void named_sync(int id, int threads) {
-  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(threads) : "memory");
+// Named barrier that also returns the OR of v over the participating threads, so every
+// thread takes the same decision.
+__device__ __forceinline__ bool named_sync_or(int id, int threads, bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+      " barrier.cta.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r) : "r"((unsigned)v), "r"(id), "r"(threads) : "memory");
+  return r != 0;
 }
 template <typename T>
 __device__ __forceinline__ T lds(const unsigned char* base, int byte_off) {
@@ -180,19 +187,21 @@ __device__ __forceinline__ T lds(const unsigned char* base, int byte_off) {
 // Fused step, TMA-staged.  CTA = BY + 2 consumer warps + 1 producer warp.  Consumer warp w
 // stands for lattice row q1 = y0 - 1 + w (warps 0 and BY + 1 are halo rows; they also compute
 // rho of the tile's two halo columns), lane l owns nodes q2 = x0 + 2 l, x0 + 2 l + 1
-// (BX = 64).  The producer's lane 0 stages raw plane p into slot (p - z0 + 1) mod NB: per
+// (BX = 64).  The producer's lane 0 stages raw plane p into slot (p - z0 + 2) mod NB: per
 // population a main box of BX columns x BY + 2 rows (rows shifted by the population's xi1, so
 // the pull of tile row w reads staged row w of every population) and two V-column halo
 // boxes at x0 - V and x0 + BX (periodic wraps in the coordinates), plus the tile's
-// coefficient rows; the slot's full mbarrier completes on the bytes, and a slot is refilled
-// only after every consumer warp has released it (empty mbarrier), so the producer runs up to
-// NB - 3 planes ahead.  Per plane u the consumers pull their populations (kept in registers)
-// and write rho into one of three rotating rho planes (step A), synchronise among themselves
-// (named barrier) and collide plane u - 1 (step B).  Face rules are reads of other staged
-// values (bounce-back / anti-bounce-back: the node's own opposite population; free: the
-// node's own population); nodes whose rule leaves the staged boxes (a halo row on a face, a
-// halo column on a q2 face, the plane below the segment) pull from global memory.  Every
-// mbarrier wait is bounded: on expiry counters[3] is raised and the CTA stops.
+// coefficient rows; the plane below the segment carries population 5 only.  The slot's full
+// mbarrier completes on the bytes, and a slot is refilled only after every consumer warp has
+// released it (empty mbarrier), so the producer runs up to NB - 3 planes ahead.  Per plane u
+// the consumers pull their populations and write rho into one of three rotating rho planes
+// (step A), synchronise among themselves (named barrier) and collide plane u - 1 (step B,
+// rows of the tile only).  Face rules are reads of other staged values (bounce-back /
+// anti-bounce-back: the node's own opposite population; free: the node's own population),
+// chosen by selects so the per-plane code has no data-dependent branches; the launch shape
+// keeps halo rows off the q1 faces and halo columns off the q2 faces.  Shared memory is
+// addressed by 32-bit offsets from the dynamic array.  Every mbarrier wait is bounded: on
+// expiry counters[3] is raised and the CTA stops.
 template <typename S, int BY>
 __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     const StepArgs<S> a, const __grid_constant__ CUtensorMap tm_main,
@@ -215,24 +224,28 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
   __shared__ int abort_flag;
   __shared__ unsigned long long t_sample;
 
+  // Programmatic dependent launch: this grid may be scheduled while the previous step drains;
+  // nothing of the previous step's output (populations, counters) is touched before its
+  // completion, and the next step may be scheduled from here on.
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * a.lz;
   const int z1 = min(z0 + a.lz, a.n3);
   const bool p2 = a.bc[2] == LBW_BC_PERIODIC, p3 = a.bc[4] == LBW_BC_PERIODIC;
 
-  // TMA destinations want 128-byte alignment: offset the shared array itself so the compiler
-  // keeps shared-space addressing
-  unsigned char* sb = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(sb);      // NB
-  unsigned long long* empty = full + NB;                                     // NB
-  unsigned char* slots = sb + 128;
-  R* rho_s = reinterpret_cast<R*>(slots + NB * SLOTB);
-  unsigned char* tabs = reinterpret_cast<unsigned char*>(rho_s) + RHOB;      // NB x TABB
+  // byte offsets from smem_raw (TMA destinations want 128-byte alignment): barriers, NB
+  // slots, three rho planes, NB coefficient blocks
+  const unsigned sbase = smem_u32(smem_raw);
+  const unsigned OFF = (128u - (sbase & 127u)) & 127u;
+  const unsigned SL = OFF + 128, RHO = SL + NB * SLOTB, TAB = RHO + RHOB;
+  auto full_at = [&](int k) { return sbase + OFF + 8u * k; };
+  auto empty_at = [&](int k) { return sbase + OFF + 8u * (NB + k); };
 
   if (tid == 0) {
     for (int k = 0; k < NB; ++k) {
-      mbar_init_count(smem_u32(&full[k]), 1);
-      mbar_init_count(smem_u32(&empty[k]), NCW);
+      mbar_init_count(full_at(k), 1);
+      mbar_init_count(empty_at(k), NCW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     probe_cnt = 0;
@@ -247,10 +260,9 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
   }
   __syncthreads();
 
-  auto wait_bar = [&](unsigned long long* bar, unsigned parity) -> bool {
-    const unsigned b = smem_u32(bar);
+  auto wait_bar = [&](unsigned bar, unsigned parity) -> bool {
     long long it = 0;
-    while (!mbar_try_wait(b, parity)) {
+    while (!mbar_try_wait(bar, parity)) {
       if (++it > kWaitLimit) {
         abort_flag = 1;
         a.counters[3] = 1;
@@ -270,26 +282,26 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       int s = 0, use = 0;
       int issued = z0 - 3;
       for (int p = z0 - 2; p <= z1 + 1; ++p) {
-        if (use > 0 && !wait_bar(&empty[s], (unsigned)((use - 1) & 1))) break;
-        const unsigned bar = smem_u32(&full[s]);
+        if (use > 0 && !wait_bar(empty_at(s), (unsigned)((use - 1) & 1))) break;
+        const unsigned bar = full_at(s);
+        const unsigned base = sbase + SL + s * SLOTB;
         const int pg = resolve(p, a.n3, p3);
         if (pg < 0) {
           mbar_expect_tx(bar, 0);
         } else if (p == z0 - 2) {  // only population 5 of this plane streams into the segment
           mbar_expect_tx(bar, (unsigned)(ROWS * BX * ES));
-          tma_load_4d(smem_u32(slots + s * SLOTB + 5 * POPB), &tm_main, x0, y0 - 1, pg, 5, bar);
+          tma_load_4d(base + 5 * POPB, &tm_main, x0, y0 - 1, pg, 5, bar);
         } else {
           const bool tab = p >= z0 && p < z1;
           mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
-          unsigned char* base = slots + s * SLOTB;
 #pragma unroll 1
           for (int i = 0; i < 7; ++i) {
             const int row = y0 - 1 - xi1_of(i);
-            tma_load_4d(smem_u32(base + i * POPB), &tm_main, x0, row, pg, i, bar);
-            if (hl) tma_load_4d(smem_u32(base + i * POPB + MB), &tm_halo, xl, row, pg, i, bar);
-            if (hr) tma_load_4d(smem_u32(base + i * POPB + MB + HB), &tm_halo, xr, row, pg, i, bar);
+            tma_load_4d(base + i * POPB, &tm_main, x0, row, pg, i, bar);
+            if (hl) tma_load_4d(base + i * POPB + MB, &tm_halo, xl, row, pg, i, bar);
+            if (hr) tma_load_4d(base + i * POPB + MB + HB, &tm_halo, xr, row, pg, i, bar);
           }
-          if (tab) tma_load_3d(smem_u32(tabs + s * TABB), &tm_tab, 0, y0, pg, bar);
+          if (tab) tma_load_3d(sbase + TAB + s * TABB, &tm_tab, 0, y0, pg, bar);
         }
         issued = p;
         if (++s == NB) { s = 0; ++use; }
@@ -297,259 +309,261 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       // drain: the last NB staged planes have landed before the CTA exits (bounded)
       for (int p = max(z0 - 2, issued - NB + 1); p <= issued; ++p) {
         const int k = p - (z0 - 2);
-        wait_bar(&full[k % NB], (unsigned)((k / NB) & 1));
+        wait_bar(full_at(k % NB), (unsigned)((k / NB) & 1));
       }
     }
   } else {  // ------------------------------------------------------------------- consumers
     const int q1 = y0 - 1 + w;
-    const int r1 = resolve(q1, a.n1, false);
     const bool interior = w >= 1 && w <= BY;
+    const bool rowin = q1 >= 0 && q1 < a.n1;  // a lattice row, not a ghost beyond a q1 face
+    const bool owner = interior && rowin;
     const int c0 = lane * NPT;
     const int q2 = x0 + c0;
-    const bool owner = interior && q1 < a.n1;
     const bool q2lo = !p2 && q2 == 0, q2hi = !p2 && q2 + NPT - 1 == a.n2 - 1;
     const R sc0 = Store<S>::kScaled ? a.w[0] : R(1), sc1 = Store<S>::kScaled ? a.w[1] : R(1);
+    auto wall = [&](int b) -> R { return b == LBW_BC_BOUNCE ? a.damping : R(-1); };
+    auto ld1 = [&](unsigned off) -> R { return Store<S>::ld_smem(reinterpret_cast<const S*>(smem_raw + off)); };
+    auto ldv = [&](unsigned off, R (&o)[NPT]) { Vec<S>::ld(reinterpret_cast<const S*>(smem_raw + off), o); };
+    auto ldr = [&](unsigned off) -> R { return *reinterpret_cast<const R*>(smem_raw + off); };
 
-    // byte offsets within a slot of this lane's vectors: pops 0, 3, 4, 5, 6 at (w, c0);
-    // pops 1 / 2 at the pull or at the q1-face rule
-    const int own = w * BX * ES + c0 * ES;
-    int o1 = POPB + own, o2 = 2 * POPB + own;
-    // the face rules of rows 0 and n1 - 1 read the staged rows next to the node: the launch
-    // shape keeps halo rows off the faces (y0 - 1 > 0 or < 0, y0 + BY != n1 - 1)
+    // offsets within a slot of this lane's vectors: pops 0, 3, 4, 5, 6 at (w, c0); pops 1 / 2
+    // at the pull or at the q1-face rule (the face rows read the staged rows next to them)
+    const unsigned own = (unsigned)(w * BX * ES + c0 * ES);
+    unsigned o1 = POPB + own, o2 = 2 * POPB + own;
     R m1 = sc1, m2 = sc1;
-    if (r1 == 0) {
+    if (rowin && q1 == 0) {
       const int b = a.bc[0];
       if (b == LBW_BC_FREE) o1 = POPB + own + BX * ES;
-      else { o1 = 2 * POPB + own - BX * ES; m1 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
+      else { o1 = 2 * POPB + own - BX * ES; m1 = sc1 * wall(b); }
     }
-    if (r1 == a.n1 - 1) {
+    if (rowin && q1 == a.n1 - 1) {
       const int b = a.bc[1];
       if (b == LBW_BC_FREE) o2 = 2 * POPB + own - BX * ES;
-      else { o2 = POPB + own + BX * ES; m2 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
+      else { o2 = POPB + own + BX * ES; m2 = sc1 * wall(b); }
     }
     // pop 3 of node c0 reads column c0 - 1 (left halo box for lane 0), pop 4 of node c0 + 1
     // reads column c0 + 2 (right halo box for lane 31)
-    const int o3e = lane == 0 ? 3 * POPB + MB + w * 16 + (V - 1) * ES : 3 * POPB + own - ES;
-    const int o4e = lane == 31 ? 4 * POPB + MB + HB + w * 16 : 4 * POPB + own + 2 * ES;
+    const unsigned o3e = lane == 0 ? 3 * POPB + MB + w * 16 + (V - 1) * ES : 3 * POPB + own - ES;
+    const unsigned o4e = lane == 31 ? 4 * POPB + MB + HB + w * 16 : 4 * POPB + own + 2 * ES;
+    // q2 faces (non-periodic q2): free copies the node's own value, walls reflect the opposite
+    const bool q2lo_free = a.bc[2] == LBW_BC_FREE, q2hi_free = a.bc[3] == LBW_BC_FREE;
+    const R q2lo_m = sc1 * wall(a.bc[2]), q2hi_m = sc1 * wall(a.bc[3]);
+    // q3 faces: slot offset and factor of populations 5 / 6 at the first / last plane
+    const unsigned f5_face = (a.bc[4] == LBW_BC_FREE ? 5 : 6) * POPB;
+    const unsigned f6_face = (a.bc[5] == LBW_BC_FREE ? 6 : 5) * POPB;
+    const R m5_face = a.bc[4] == LBW_BC_FREE ? sc1 : sc1 * wall(a.bc[4]);
+    const R m6_face = a.bc[5] == LBW_BC_FREE ? sc1 : sc1 * wall(a.bc[5]);
 
-    // halo column node of a halo warp: warp 0 lane l -> (y0 + l, x0 - 1), warp BY+1 -> x0 + BX
-    const bool hcol = !interior && lane < BY;
-    const int hq1 = y0 + lane, hq2 = (w == 0) ? x0 - 1 : x0 + BX;
-    const int hr1 = resolve(hq1, a.n1, false), hr2 = resolve(hq2, a.n2, p2);
-    int h0 = 0, h1 = 0, h2 = 0, h3 = 0, h4 = 0, h56 = 0;  // byte offsets in a slot
+    // halo column node of a halo warp: warp 0 lane l -> (y0 + l, x0 - 1), warp BY+1 ->
+    // (y0 + l, x0 + BX), lanes l < BY; the other lanes mirror lane BY - 1 and store nothing
+    const bool hwarp = !interior;
+    const int hl = lane < BY ? lane : BY - 1;
+    const int hq1 = y0 + hl, hq2 = (w == 0) ? x0 - 1 : x0 + BX;
+    const bool hcol = hwarp && lane < BY;
+    const bool hin = hq1 < a.n1 && (p2 || (hq2 >= 0 && hq2 < a.n2));
+    unsigned h0, h1, h2, h3, h4;
     R hm1 = sc1, hm2 = sc1;
-    if (hcol) {
-      const int hw = lane + 1;
+    {
+      const int hw = hl + 1;
       // column -1 lives in the left halo box (index V - 1), column BX in the right one (0)
-      const int hbox = (w == 0) ? MB : MB + HB, hcolb = (w == 0) ? (V - 1) * ES : 0;
-      auto hat = [&](int pop, int row) { return pop * POPB + hbox + row * 16 + hcolb; };
+      const unsigned hbox = (w == 0) ? MB : MB + HB, hcolb = (w == 0) ? (V - 1) * ES : 0;
+      auto hat = [&](int pop, int row) { return (unsigned)(pop * POPB) + hbox + row * 16 + hcolb; };
       h0 = hat(0, hw);
       h1 = hat(1, hw);
       h2 = hat(2, hw);
-      h56 = hat(0, hw) - 0 * POPB;  // pop offset added per plane
       // pop 3 from column -2 / BX - 1, pop 4 from column 0 / BX + 1
       h3 = (w == 0) ? 3 * POPB + MB + hw * 16 + (V - 2) * ES : 3 * POPB + hw * BX * ES + (BX - 1) * ES;
       h4 = (w == 0) ? 4 * POPB + hw * BX * ES : 4 * POPB + MB + HB + hw * 16 + ES;
-      if (hr1 == 0) {
+      if (hq1 == 0) {
         const int b = a.bc[0];
         if (b == LBW_BC_FREE) h1 = hat(1, hw + 1);
-        else { h1 = hat(2, hw - 1); hm1 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
+        else { h1 = hat(2, hw - 1); hm1 = sc1 * wall(b); }
       }
-      if (hr1 == a.n1 - 1) {
+      if (hq1 == a.n1 - 1) {
         const int b = a.bc[1];
         if (b == LBW_BC_FREE) h2 = hat(2, hw - 1);
-        else { h2 = hat(1, hw + 1); hm2 = sc1 * (b == LBW_BC_BOUNCE ? a.damping : R(-1)); }
+        else { h2 = hat(1, hw + 1); hm2 = sc1 * wall(b); }
       }
-      // a halo column is never on a q2 face (the q2 extent is a multiple of BX), so its own
-      // q2 pulls are plain
     }
-    const int hrho = (lane + 1) * PW + ((w == 0) ? 1 : BX + 2);
+    const unsigned hrho = (unsigned)(((hl + 1) * PW + ((w == 0) ? 1 : BX + 2)) * RS);
+    const unsigned myrho = (unsigned)((w * PW + 2 + c0) * RS);
+
+    // probes of this warp's row (recorded while the sample counter is below capacity)
+    bool has_probe = false;
+    if (owner && t_sample < (unsigned long long)a.cap)
+      for (int s = 0; s < probe_cnt; ++s) has_probe |= a.probe_q[3 * probe_list[s]] == q1;
 
     R fA[7][NPT], fB[7][NPT], rA[NPT], rB[NPT], rC[NPT];
     const long long n12 = (long long)a.n1 * a.n2;
     S* const dst_z0 = a.fout + node(owner ? q1 : 0, q2, z0, a.n1, a.n2);
 
     // step A of pulled plane u: populations into f, rho into rr and (wr) the rho plane
-#define LBW_STEP_A(u, f, rr, slm, sl0, slp, rbu, wr)                                              \
-    do {                                                                                          \
-      const int r3_ = resolve((u), a.n3, p3);                                                     \
-      const unsigned char* S0 = slots + (sl0) * SLOTB;                                            \
-      const unsigned char* Sm = slots + (slm) * SLOTB;                                            \
-      const unsigned char* Sp = slots + (slp) * SLOTB;                                            \
-      const unsigned char* B5 = Sm + 5 * POPB;                                                    \
-      const unsigned char* B6 = Sp + 6 * POPB;                                                    \
-      R m5_ = sc1, m6_ = sc1;                                                                     \
-      if (!p3 && r3_ == 0) {                                                                      \
-        const int b_ = a.bc[4];                                                                   \
-        if (b_ == LBW_BC_FREE) B5 = S0 + 5 * POPB;                                                \
-        else { B5 = S0 + 6 * POPB; m5_ = sc1 * (b_ == LBW_BC_BOUNCE ? a.damping : R(-1)); }       \
-      }                                                                                           \
-      if (!p3 && r3_ == a.n3 - 1) {                                                               \
-        const int b_ = a.bc[5];                                                                   \
-        if (b_ == LBW_BC_FREE) B6 = S0 + 6 * POPB;                                                \
-        else { B6 = S0 + 5 * POPB; m6_ = sc1 * (b_ == LBW_BC_BOUNCE ? a.damping : R(-1)); }       \
-      }                                                                                           \
-      if (r3_ < 0 || r1 < 0) {                                                                    \
-        rr[0] = R(0); rr[1] = R(0);                                                               \
-      } else {                                                                                    \
-        R t3_[NPT], t4_[NPT];                                                                     \
-        Vec<S>::ld(reinterpret_cast<const S*>(S0 + own), f[0]);                                   \
-        Vec<S>::ld(reinterpret_cast<const S*>(S0 + o1), f[1]);                                    \
-        Vec<S>::ld(reinterpret_cast<const S*>(S0 + o2), f[2]);                                    \
-        Vec<S>::ld(reinterpret_cast<const S*>(S0 + 3 * POPB + own), t3_);                         \
-        Vec<S>::ld(reinterpret_cast<const S*>(S0 + 4 * POPB + own), t4_);                         \
-        Vec<S>::ld(reinterpret_cast<const S*>(B5 + own), f[5]);                                   \
-        Vec<S>::ld(reinterpret_cast<const S*>(B6 + own), f[6]);                                   \
-        f[3][0] = sc1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + o3e));                  \
-        f[3][1] = sc1 * t3_[0];                                                                   \
-        f[4][0] = sc1 * t4_[1];                                                                   \
-        f[4][1] = sc1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + o4e));                  \
-        _Pragma("unroll") for (int k_ = 0; k_ < NPT; ++k_) {                                    \
-          f[0][k_] *= sc0; f[1][k_] *= m1; f[2][k_] *= m2; f[5][k_] *= m5_; f[6][k_] *= m6_;      \
-        }                                                                                         \
-        if (q2lo) {                                                                               \
-          const int b_ = a.bc[2];                                                                 \
-          f[3][0] = sc1 * (b_ == LBW_BC_FREE ? t3_[0] : (b_ == LBW_BC_BOUNCE ? a.damping : R(-1)) * t4_[0]); \
-        }                                                                                         \
-        if (q2hi) {                                                                               \
-          const int b_ = a.bc[3];                                                                 \
-          f[4][1] = sc1 * (b_ == LBW_BC_FREE ? t4_[1] : (b_ == LBW_BC_BOUNCE ? a.damping : R(-1)) * t3_[1]); \
-        }                                                                                         \
-        _Pragma("unroll") for (int k_ = 0; k_ < NPT; ++k_)                                      \
-          rr[k_] = ((f[0][k_] + f[1][k_]) + (f[2][k_] + f[3][k_])) + ((f[4][k_] + f[5][k_]) + f[6][k_]); \
-      }                                                                                           \
-      if (wr) {                                                                                   \
-        R* out_ = rho_s + (rbu) * PS;                                                             \
-        RVec<R>::st(out_ + w * PW + 2 + c0, rr);                                                  \
-        if (hcol) {                                                                               \
-          R h_ = R(0);                                                                            \
-          if (r3_ >= 0 && hr1 >= 0 && hr2 >= 0) {                                                 \
-            R g_[7];                                                                              \
-            g_[0] = sc0 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h0));                 \
-            g_[1] = hm1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h1));                 \
-            g_[2] = hm2 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h2));                 \
-            g_[3] = sc1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h3));                 \
-            g_[4] = sc1 * Store<S>::ld_smem(reinterpret_cast<const S*>(S0 + h4));                 \
-            g_[5] = m5_ * Store<S>::ld_smem(reinterpret_cast<const S*>(B5 + h56));                \
-            g_[6] = m6_ * Store<S>::ld_smem(reinterpret_cast<const S*>(B6 + h56));                \
-            h_ = ((g_[0] + g_[1]) + (g_[2] + g_[3])) + ((g_[4] + g_[5]) + g_[6]);                 \
-          }                                                                                       \
-          out_[hrho] = h_;                                                                        \
-        }                                                                                         \
-      }                                                                                           \
-    } while (0)
+    auto stepA = [&](int u, R (&f)[7][NPT], R (&rr)[NPT], int slm, int sl0, int slp, int rbu,
+                     bool wr) {
+      const bool zlo = !p3 && u == 0, zhi = !p3 && u == a.n3 - 1;
+      const bool zghost = !p3 && (u < 0 || u >= a.n3);
+      const unsigned S0 = SL + sl0 * SLOTB;
+      const unsigned B5 = zlo ? S0 + f5_face : SL + slm * SLOTB + 5 * POPB;
+      const unsigned B6 = zhi ? S0 + f6_face : SL + slp * SLOTB + 6 * POPB;
+      const R m5 = zlo ? m5_face : sc1, m6 = zhi ? m6_face : sc1;
+      R t3[NPT], t4[NPT];
+      ldv(S0 + own, f[0]);
+      ldv(S0 + o1, f[1]);
+      ldv(S0 + o2, f[2]);
+      ldv(S0 + 3 * POPB + own, t3);
+      ldv(S0 + 4 * POPB + own, t4);
+      ldv(B5 + own, f[5]);
+      ldv(B6 + own, f[6]);
+      f[3][0] = sc1 * ld1(S0 + o3e);
+      f[3][1] = sc1 * t3[0];
+      f[4][0] = sc1 * t4[1];
+      f[4][1] = sc1 * ld1(S0 + o4e);
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        if (Store<S>::kScaled) f[0][k] *= sc0;
+        f[1][k] *= m1; f[2][k] *= m2; f[5][k] *= m5; f[6][k] *= m6;
+      }
+      if (!p2) {
+        f[3][0] = q2lo ? (q2lo_free ? sc1 * t3[0] : q2lo_m * t4[0]) : f[3][0];
+        f[4][1] = q2hi ? (q2hi_free ? sc1 * t4[1] : q2hi_m * t3[1]) : f[4][1];
+      }
+      const bool ghost = zghost || !rowin;
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const R s = ((f[0][k] + f[1][k]) + (f[2][k] + f[3][k])) + ((f[4][k] + f[5][k]) + f[6][k]);
+        rr[k] = ghost ? R(0) : s;
+      }
+      if (wr) {
+        const unsigned pl = RHO + rbu * (PS * RS);
+        RVec<R>::st(reinterpret_cast<R*>(smem_raw + pl + myrho), rr);
+        if (hwarp) {
+          R g[7];
+          g[0] = sc0 * ld1(S0 + h0);
+          g[1] = hm1 * ld1(S0 + h1);
+          g[2] = hm2 * ld1(S0 + h2);
+          g[3] = sc1 * ld1(S0 + h3);
+          g[4] = sc1 * ld1(S0 + h4);
+          g[5] = m5 * ld1(B5 + h0);  // h0 addresses population 0: B5 / B6 add their own
+          g[6] = m6 * ld1(B6 + h0);
+          const R h = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+          if (hcol) *reinterpret_cast<R*>(smem_raw + pl + hrho) = (hin && !zghost) ? h : R(0);
+        }
+      }
+    };
 
-    // step B: collide plane z with populations fc, rho (rp, rc, rn)
-#define LBW_STEP_B(zc, fc, rp, rc, rn, slz, rbz)                                                   \
-    do {                                                                                          \
-      const R* cur_ = rho_s + (rbz) * PS + w * PW + 2 + c0;                                       \
-      R ru_[NPT], rd_[NPT];                                                                       \
-      RVec<R>::ld(cur_ + PW, ru_);                                                                \
-      RVec<R>::ld(cur_ - PW, rd_);                                                                \
-      const R rl0_ = q2lo ? a.s2lo * rc[0] : cur_[-1];                                            \
-      const R rr1_ = q2hi ? a.s2hi * rc[1] : cur_[2];                                             \
-      const R rl_[NPT] = {rl0_, rc[0]}, rrr_[NPT] = {rc[1], rr1_};                                \
-      const unsigned char* T_ = tabs + (slz) * TABB + (w - 1) * T_SLOTS * RS;                    \
-      R c_[T_SLOTS];                                                                              \
-      _Pragma("unroll") for (int k_ = 0; k_ < T_SLOTS; k_ += 4) {                               \
-        if (RS == 4) {                                                                            \
-          const float4 v_ = lds<float4>(T_, k_ * RS);                                             \
-          c_[k_] = v_.x; c_[k_ + 1] = v_.y; c_[k_ + 2] = v_.z; c_[k_ + 3] = v_.w;                 \
-        } else {                                                                                  \
-          const double2 v0_ = lds<double2>(T_, k_ * RS), v1_ = lds<double2>(T_, (k_ + 2) * RS);   \
-          c_[k_] = v0_.x; c_[k_ + 1] = v0_.y; c_[k_ + 2] = v1_.x; c_[k_ + 3] = v1_.y;             \
-        }                                                                                         \
-      }                                                                                           \
-      _Pragma("unroll") for (int k_ = 0; k_ < NPT; ++k_) {                                      \
-        const R rho_ = rc[k_];                                                                    \
-        const R D1_ = c_[T_A1P] * ru_[k_] - c_[T_A1M] * rd_[k_] + c_[T_C13P] * rn[k_] -           \
-                      c_[T_C13M] * rp[k_] + c_[T_S1] * rho_;                                      \
-        const R D3_ = c_[T_B13P] * ru_[k_] - c_[T_B13M] * rd_[k_] + c_[T_C33P] * rn[k_] -         \
-                      c_[T_C33M] * rp[k_] + c_[T_S3] * rho_;                                      \
-        const R D2_ = c_[T_H22] * (rrr_[k_] - rl_[k_]);                                           \
-        const R j1_ = (fc[1][k_] - fc[2][k_]) + R(0.5) * (c_[T_MG1] * rho_ - D1_);                \
-        const R j2_ = (fc[3][k_] - fc[4][k_]) - R(0.5) * D2_;                                     \
-        const R j3_ = (fc[5][k_] - fc[6][k_]) + R(0.5) * (c_[T_MG3] * rho_ - D3_);                \
-        const R e_ = a.cs2 * rho_;                                                                \
-        fc[0][k_] = a.two_w0 * rho_ - fc[0][k_];                                                  \
-        fc[1][k_] = e_ + j1_ - fc[1][k_];                                                         \
-        fc[2][k_] = e_ - j1_ - fc[2][k_];                                                         \
-        fc[3][k_] = e_ + j2_ - fc[3][k_];                                                         \
-        fc[4][k_] = e_ - j2_ - fc[4][k_];                                                         \
-        fc[5][k_] = e_ + j3_ - fc[5][k_];                                                         \
-        fc[6][k_] = e_ - j3_ - fc[6][k_];                                                         \
-      }                                                                                           \
-      S* dst_ = dst_z0 + (long long)((zc) - z0) * n12;                                            \
-      _Pragma("unroll") for (int i_ = 0; i_ < 7; ++i_) {                                        \
-        if (Store<S>::kScaled) { fc[i_][0] *= a.inv_w[i_]; fc[i_][1] *= a.inv_w[i_]; }            \
-        Vec<S>::st(dst_, fc[i_]);                                                                 \
-        dst_ += a.nn;                                                                             \
-      }                                                                                           \
-      if (probe_cnt > 0 && t_sample < (unsigned long long)a.cap) {                                \
-        for (int s2_ = 0; s2_ < probe_cnt; ++s2_) {                                               \
-          const int k_ = probe_list[s2_];                                                         \
-          const int dq_ = a.probe_q[3 * k_ + 1] - q2;                                             \
-          if (a.probe_q[3 * k_] == q1 && dq_ >= 0 && dq_ < NPT && a.probe_q[3 * k_ + 2] == (zc))   \
-            a.series[(long long)k_ * a.cap + t_sample] =                                          \
-                (double)(dq_ == 0 ? rc[0] : rc[1]) * (double)c_[T_INVSG];                         \
-        }                                                                                         \
-      }                                                                                           \
-    } while (0)
+    // step B: collide plane zc with populations fc, rho (rp, rc, rn)
+    auto stepB = [&](int zc, R (&fc)[7][NPT], const R (&rp)[NPT], const R (&rc)[NPT],
+                     const R (&rn)[NPT], int slz, int rbz) {
+      const unsigned cur = RHO + rbz * (PS * RS) + myrho;
+      R ru[NPT], rd[NPT];
+      RVec<R>::ld(reinterpret_cast<const R*>(smem_raw + cur + PW * RS), ru);
+      RVec<R>::ld(reinterpret_cast<const R*>(smem_raw + cur - PW * RS), rd);
+      const R lft = ldr(cur - RS), rgt = ldr(cur + 2 * RS);
+      const R rl[NPT] = {q2lo ? a.s2lo * rc[0] : lft, rc[0]};
+      const R rrt[NPT] = {rc[1], q2hi ? a.s2hi * rc[1] : rgt};
+      const unsigned T = TAB + slz * TABB + (w - 1) * (T_SLOTS * RS);
+      R c[T_SLOTS];
+#pragma unroll
+      for (int k = 0; k < T_SLOTS; k += 4) {
+        if (RS == 4) {
+          const float4 v = *reinterpret_cast<const float4*>(smem_raw + T + k * RS);
+          c[k] = v.x; c[k + 1] = v.y; c[k + 2] = v.z; c[k + 3] = v.w;
+        } else {
+          const double2 v0 = *reinterpret_cast<const double2*>(smem_raw + T + k * RS);
+          const double2 v1 = *reinterpret_cast<const double2*>(smem_raw + T + (k + 2) * RS);
+          c[k] = v0.x; c[k + 1] = v0.y; c[k + 2] = v1.x; c[k + 3] = v1.y;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const R rho = rc[k];
+        const R D1 = c[T_A1P] * ru[k] - c[T_A1M] * rd[k] + c[T_C13P] * rn[k] - c[T_C13M] * rp[k] +
+                     c[T_S1] * rho;
+        const R D3 = c[T_B13P] * ru[k] - c[T_B13M] * rd[k] + c[T_C33P] * rn[k] - c[T_C33M] * rp[k] +
+                     c[T_S3] * rho;
+        const R D2 = c[T_H22] * (rrt[k] - rl[k]);
+        const R j1 = (fc[1][k] - fc[2][k]) + R(0.5) * (c[T_MG1] * rho - D1);
+        const R j2 = (fc[3][k] - fc[4][k]) - R(0.5) * D2;
+        const R j3 = (fc[5][k] - fc[6][k]) + R(0.5) * (c[T_MG3] * rho - D3);
+        const R e = a.cs2 * rho;
+        fc[0][k] = a.two_w0 * rho - fc[0][k];
+        fc[1][k] = e + j1 - fc[1][k];
+        fc[2][k] = e - j1 - fc[2][k];
+        fc[3][k] = e + j2 - fc[3][k];
+        fc[4][k] = e - j2 - fc[4][k];
+        fc[5][k] = e + j3 - fc[5][k];
+        fc[6][k] = e - j3 - fc[6][k];
+      }
+      S* dst = dst_z0 + (long long)(zc - z0) * n12;
+#pragma unroll
+      for (int i = 0; i < 7; ++i) {
+        if (Store<S>::kScaled) { fc[i][0] *= a.inv_w[i]; fc[i][1] *= a.inv_w[i]; }
+        Vec<S>::st(dst, fc[i]);
+        dst += a.nn;
+      }
+      if (has_probe) {
+        for (int s = 0; s < probe_cnt; ++s) {
+          const int k = probe_list[s];
+          const int dq = a.probe_q[3 * k + 1] - q2;
+          if (a.probe_q[3 * k] == q1 && dq >= 0 && dq < NPT && a.probe_q[3 * k + 2] == zc)
+            a.series[(long long)k * a.cap + t_sample] = (double)(dq == 0 ? rc[0] : rc[1]) * (double)c[T_INVSG];
+        }
+      }
+    };
 
     // rho of plane z0 - 1 at the own nodes, from the staged planes z0 - 2 (population 5 only),
     // z0 - 1 and z0; then step A of plane z0
-    bool ok = wait_bar(&full[0], 0) && wait_bar(&full[1], 0) && wait_bar(&full[2], 0);
-    if (ok && owner) LBW_STEP_A(z0 - 1, fB, rA, 0, 1, 2, 2, false);
-    if (lane == 0) mbar_arrive(smem_u32(&empty[0]));  // plane z0 - 2 is no longer needed
-    ok = ok && wait_bar(&full[3], 0);
-    if (ok) LBW_STEP_A(z0, fA, rB, 1, 2, 3, 0, true);
-    if (lane == 0) mbar_arrive(smem_u32(&empty[1]));  // nor is plane z0 - 1
-    named_sync(1, NCW * 32);
-    if (abort_flag) ok = false;
-    int z = z0;
+    bool ok = wait_bar(full_at(0), 0) && wait_bar(full_at(1), 0) && wait_bar(full_at(2), 0);
+    if (ok && owner) stepA(z0 - 1, fB, rA, 0, 1, 2, 2, false);
+    if (lane == 0) mbar_arrive(empty_at(0));  // plane z0 - 2 is no longer needed
+    ok = ok && wait_bar(full_at(3), 0);
+    if (ok) stepA(z0, fA, rB, 1, 2, 3, 0, true);
+    if (lane == 0) mbar_arrive(empty_at(1));  // nor is plane z0 - 1
+    ok = !named_sync_or(1, NCW * 32, !ok || abort_flag);
     // slots of raw planes z, z + 1, z + 2 (plane z0 - 2 sits in slot 0) and the fill count of
-    // plane z + 2's slot, advanced plane by plane
-    // rho planes rotate through three buffers: a warp writing plane z + 1's buffer has passed
-    // the barrier that follows every read of that buffer (plane z - 2); the rows of plane
-    // z0 - 1 written into buffer 2 above are never read
+    // plane z + 2's slot, advanced plane by plane.  rho planes rotate through three buffers: a
+    // warp writing plane z + 1's buffer has passed the barrier that follows every read of that
+    // buffer (plane z - 2); the rows of plane z0 - 1 in buffer 2 are never written or read.
     int sz = 2, s1 = 3, s2 = 4, u2 = 0, rbz = 0, rb1 = 1;
-#define LBW_ADVANCE()                                                                             \
-    do {                                                                                          \
-      rbz = rb1;                                                                                  \
-      rb1 = rb1 == 2 ? 0 : rb1 + 1;                                                               \
-      sz = s1;                                                                                    \
-      s1 = s2;                                                                                    \
-      s2 = s2 == NB - 1 ? 0 : s2 + 1;                                                             \
-      if (s2 == 0) ++u2;                                                                          \
-    } while (0)
-    // iteration z: raw plane z + 2 in, A(z + 1), barrier, B(z), release raw plane z
-#define LBW_ITER(zz, fc, fn, rp, rc, rn)                                                          \
-    do {                                                                                          \
-      if (!abort_flag && !wait_bar(&full[s2], (unsigned)(u2 & 1))) ok = false;                    \
-      if (ok && !abort_flag) LBW_STEP_A((zz) + 1, fn, rn, sz, s1, s2, rb1, true);                 \
-      named_sync(1, NCW * 32);                                                                    \
-      if (abort_flag) ok = false;                                                                 \
-      if (ok && owner) LBW_STEP_B((zz), fc, rp, rc, rn, sz, rbz);                                 \
-      /* raw plane zz (pop 5 of A(zz + 1), coefficient rows of B(zz)) is no longer needed */      \
-      if (lane == 0) mbar_arrive(smem_u32(&empty[sz]));                                           \
-      LBW_ADVANCE();                                                                              \
-    } while (0)
-    for (; ok && z + 1 < z1; z += 2) {
-      LBW_ITER(z, fA, fB, rA, rB, rC);
-      if (!ok) break;
-      LBW_ITER(z + 1, fB, fA, rB, rC, rA);
-      // next pair expects rho(z+1), rho(z+2) in rA, rB
-      for (int k = 0; k < NPT; ++k) {
-        const R t = rA[k];
-        rA[k] = rC[k];
-        rB[k] = t;
+    auto advance = [&]() {
+      rbz = rb1;
+      rb1 = rb1 == 2 ? 0 : rb1 + 1;
+      sz = s1;
+      s1 = s2;
+      s2 = s2 == NB - 1 ? 0 : s2 + 1;
+      if (s2 == 0) ++u2;
+    };
+    // iteration z: raw plane z + 2 in, A(z + 1), barrier, B(z), release raw plane z.  Every
+    // warp passes the same barriers; the barrier ORs the warps' abort states (a timed-out wait
+    // here, or the producer's flag), so all warps leave after the same iteration.
+    auto iter = [&](int zz, R (&fc)[7][NPT], R (&fn)[7][NPT], const R (&rp)[NPT],
+                    const R (&rc)[NPT], R (&rn)[NPT], bool collide) {
+      const bool in = wait_bar(full_at(s2), (unsigned)(u2 & 1));
+      if (in) stepA(zz + 1, fn, rn, sz, s1, s2, rb1, true);
+      const bool go = !named_sync_or(1, NCW * 32, !in || abort_flag);
+      if (go && collide) stepB(zz, fc, rp, rc, rn, sz, rbz);
+      if (lane == 0) mbar_arrive(empty_at(sz));  // raw plane zz is no longer needed
+      advance();
+      return go;
+    };
+    int z = z0;
+    if (!owner) {  // halo rows and rows beyond the lattice: rho only
+      for (; ok && z < z1; ++z) ok = iter(z, fA, fB, rA, rB, rC, false);
+    } else {
+      for (; ok && z + 1 < z1; z += 2) {
+        ok = iter(z, fA, fB, rA, rB, rC, true);
+        if (!ok) break;
+        ok = iter(z + 1, fB, fA, rB, rC, rA, true);
+        // next pair expects rho(z+1), rho(z+2) in rA, rB
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+          const R t = rA[k];
+          rA[k] = rC[k];
+          rB[k] = t;
+        }
       }
+      if (ok && z < z1) ok = iter(z, fA, fB, rA, rB, rC, true);
     }
-    if (ok && z < z1) LBW_ITER(z, fA, fB, rA, rB, rC);
-#undef LBW_ITER
-#undef LBW_ADVANCE
-#undef LBW_STEP_A
-#undef LBW_STEP_B
   }
 
   __syncthreads();
@@ -611,11 +625,22 @@ cudaError_t launch_step_t(Grid* g, int src) {
   StepArgs<S> a = make_args<S>(g, src);
   if (g->tma_by > 0) {
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(g->tmaps);
-    const dim3 block(32, g->tma_by + 3);
-    if (g->tma_by == 7)
-      step_tma_kernel<S, 7><<<g->grid_dim, block, tma_smem_bytes<S, 7>(), g->stream>>>(a, m[2 * src], m[2 * src + 1], m[4]);
-    else
-      step_tma_kernel<S, 4><<<g->grid_dim, block, tma_smem_bytes<S, 4>(), g->stream>>>(a, m[2 * src], m[2 * src + 1], m[4]);
+    // consecutive steps overlap launch and prologue with the previous step's tail
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g->grid_dim;
+    cfg.blockDim = dim3(32, g->tma_by + 3);
+    cfg.stream = g->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (g->tma_by == 7) {
+      cfg.dynamicSmemBytes = tma_smem_bytes<S, 7>();
+      return cudaLaunchKernelEx(&cfg, step_tma_kernel<S, 7>, a, m[2 * src], m[2 * src + 1], m[4]);
+    }
+    cfg.dynamicSmemBytes = tma_smem_bytes<S, 4>();
+    return cudaLaunchKernelEx(&cfg, step_tma_kernel<S, 4>, a, m[2 * src], m[2 * src + 1], m[4]);
   } else {
     dim3 block(g->bx, g->by);
     size_t smem = 3 * (size_t)(g->bx + 2) * (g->by + 2) * sizeof(R);
