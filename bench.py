@@ -204,6 +204,9 @@ def main():
                     help="time steps per benchmark step (default: the workload's 20000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="cylinder", choices=["cylinder", "disk", "trumpet", "torus"])
+    ap.add_argument("--vs-f64", action="store_true",
+                    help="after the timed region, rerun the workload with FP64 storage on the "
+                         "GPU and report the field and mode-frequency deviations")
     ap.add_argument("--prec", default=None, choices=["f64", "f32", "f16s", "bf16s"],
                     help="storage override (default: the workload's own)")
     args = ap.parse_args()
@@ -312,6 +315,9 @@ def main():
     spectrum_launches = 2 + int(math.log2(M)) + 5
     launches = args.steps * (lbm_steps + spectrum_launches)
 
+    accuracy = None
+    if args.vs_f64 and rank == 0:
+        accuracy = f64_deviation(lbw, wl, lbm_steps, grid, sh)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -344,10 +350,40 @@ def main():
         "gpu_launches": launches,
         "spectrum_peaks": [round(float(x), 6) for x in freqs] if freqs is not None else None,
     }
+    if accuracy is not None:
+        line["vs_f64"] = accuracy
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def f64_deviation(lbw, wl, lbm_steps, grid, stream_handle, k=8):
+    """The same run with FP64 storage and arithmetic on the GPU (the FP64 kernels match the FP64
+    oracle to 1e-11 on the parity grids) as the reference at full size: relative L2 of the
+    final P field and the relative deviation of the k strongest spectral peaks (rad / step)
+    of the summed probes, matched in frequency order."""
+    spec64 = wl.spec.with_(prec=W.PREC_F64)
+    ref = lbw.Grid(spec64, stream=stream_handle)
+    out = {}
+    try:
+        runs = []
+        for g in (grid, ref):
+            g.init(wl.pulses)
+            g.set_probes(wl.probes, lbm_steps)
+            g.step(lbm_steps)
+            f, _ = g.spectrum(-1, k)
+            runs.append((np.sort(np.asarray(f)), g.get_P()))
+        (fa, Pa), (fb, Pb) = runs
+        n = min(len(fa), len(fb))
+        out["field_rel_l2"] = float(np.linalg.norm(Pa - Pb) / np.linalg.norm(Pb))
+        out["mode_freq_max_rel"] = float(np.max(np.abs(fa[:n] - fb[:n]) / fb[:n])) if n else None
+        out["modes_compared"] = int(n)
+        out["peaks_f64"] = [round(float(x), 7) for x in fb[:n]]
+        out["time_steps"] = lbm_steps
+    finally:
+        ref.close()
+    return out
 
 
 PROFILE = os.path.join(ROOT, "profiles", "step_tma_kernel_cylinder_128x128x256_f32.md")

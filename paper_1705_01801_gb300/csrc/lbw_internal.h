@@ -49,6 +49,7 @@ struct Grid {
   // launch shape of the step kernel
   int bx = 0, by = 0, lz = 0;
   int tma_by = 0;          // 0: register-pipelined kernel; 4 or 7: TMA tile kernel rows
+  int tma_npt = 2;         // TMA tile kernel: nodes per lane (tile width 32 x tma_npt)
   alignas(64) unsigned char tmaps[5 * 128];  // tensor maps: f[0] main/halo, f[1] main/halo, table
   dim3 grid_dim;
   // captured step chains, one per parity of the starting buffer

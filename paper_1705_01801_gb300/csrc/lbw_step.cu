@@ -50,73 +50,86 @@ __global__ void __launch_bounds__(512) step_kernel(const StepArgs<S> a) {
 
 __device__ __forceinline__ int xi1_of(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
 
-// Two consecutive nodes along q2 per lane: 8-byte FP32 / 4-byte 16-bit / 16-byte FP64
-// vectors.
-template <typename S> struct Vec;
-template <> struct Vec<float> {
-  __device__ static void ld(const float* p, float o[2]) {
+// N consecutive nodes along q2 per lane, moved as one vector: FP32 8 / 16 bytes, FP64 16
+// bytes, 16-bit formats 4 / 8 bytes (converted to and from FP32 in pairs).
+template <typename S, int N> struct VecN;
+template <> struct VecN<float, 2> {
+  __device__ static void ld(const float* p, float (&o)[2]) {
     const float2 v = *reinterpret_cast<const float2*>(p);
     o[0] = v.x; o[1] = v.y;
   }
-  __device__ static void st(float* p, const float o[2]) {
+  __device__ static void st(float* p, const float (&o)[2]) {
     *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
   }
 };
-template <> struct Vec<double> {
-  __device__ static void ld(const double* p, double o[2]) {
+template <> struct VecN<float, 4> {
+  __device__ static void ld(const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  __device__ static void st(float* p, const float (&o)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+};
+template <> struct VecN<double, 2> {
+  __device__ static void ld(const double* p, double (&o)[2]) {
     const double2 v = *reinterpret_cast<const double2*>(p);
     o[0] = v.x; o[1] = v.y;
   }
-  __device__ static void st(double* p, const double o[2]) {
+  __device__ static void st(double* p, const double (&o)[2]) {
     *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
   }
 };
-template <> struct Vec<__half> {
-  __device__ static void ld(const __half* p, float o[2]) {
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(p));
+// 16-bit pairs <-> float2
+__device__ __forceinline__ float2 to_f2(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ float2 to_f2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+template <typename P> __device__ __forceinline__ P from_f2(float a, float b);
+template <> __device__ __forceinline__ __half2 from_f2<__half2>(float a, float b) { return __floats2half2_rn(a, b); }
+template <> __device__ __forceinline__ __nv_bfloat162 from_f2<__nv_bfloat162>(float a, float b) {
+  return __floats2bfloat162_rn(a, b);
+}
+template <typename S> struct Pair16;
+template <> struct Pair16<__half> { using T = __half2; };
+template <> struct Pair16<__nv_bfloat16> { using T = __nv_bfloat162; };
+template <typename S> struct Vec16 {
+  using P = typename Pair16<S>::T;
+  __device__ static void ld(const S* p, float (&o)[2]) {
+    const float2 a = to_f2(*reinterpret_cast<const P*>(p));
     o[0] = a.x; o[1] = a.y;
   }
-  __device__ static void st(__half* p, const float o[2]) {
-    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(o[0], o[1]);
+  __device__ static void st(S* p, const float (&o)[2]) {
+    *reinterpret_cast<P*>(p) = from_f2<P>(o[0], o[1]);
+  }
+  __device__ static void ld(const S* p, float (&o)[4]) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    const float2 a = to_f2(*reinterpret_cast<const P*>(&u.x)), b = to_f2(*reinterpret_cast<const P*>(&u.y));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  __device__ static void st(S* p, const float (&o)[4]) {
+    const P a = from_f2<P>(o[0], o[1]), b = from_f2<P>(o[2], o[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned*>(&a);
+    u.y = *reinterpret_cast<const unsigned*>(&b);
+    *reinterpret_cast<uint2*>(p) = u;
   }
 };
-template <> struct Vec<__nv_bfloat16> {
-  __device__ static void ld(const __nv_bfloat16* p, float o[2]) {
-    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
-    o[0] = a.x; o[1] = a.y;
-  }
-  __device__ static void st(__nv_bfloat16* p, const float o[2]) {
-    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(o[0], o[1]);
-  }
-};
-template <typename R> struct RVec;
-template <> struct RVec<float> {
-  __device__ static void ld(const float* p, float o[2]) { Vec<float>::ld(p, o); }
-  __device__ static void st(float* p, const float o[2]) { Vec<float>::st(p, o); }
-};
-template <> struct RVec<double> {
-  __device__ static void ld(const double* p, double o[2]) { Vec<double>::ld(p, o); }
-  __device__ static void st(double* p, const double o[2]) { Vec<double>::st(p, o); }
-};
+template <int N> struct VecN<__half, N> : Vec16<__half> {};
+template <int N> struct VecN<__nv_bfloat16, N> : Vec16<__nv_bfloat16> {};
+
+// Paired FP32 arithmetic (one instruction for two lanes' values of a node pair), the same
+// IEEE round-to-nearest operations as the scalar forms.
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 add2(float2 x, float2 y) { return __fadd2_rn(x, y); }
+__device__ __forceinline__ float2 mul2(float2 x, float2 y) { return __fmul2_rn(x, y); }
+__device__ __forceinline__ float2 fma2(float2 x, float2 y, float2 z) { return __ffma2_rn(x, y, z); }
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, bc2(-1.f), x); }
 
 // ---------------------------------------------------------------- TMA tile kernel -------
 //
-// Raw post-collision planes are staged by the Tensor Memory Accelerator: per plane one elected
-// thread issues, for every population, a main box (BX columns x BY + 2 rows, rows shifted by
-// the population's xi1 so the pull of tile row w reads staged row w of every population) and
-// two V-column halo boxes at x0 - V and x0 + BX (periodic wraps resolved in the coordinates),
-// plus the tile's coefficient rows; all complete on the slot's mbarrier.  NB = 3 + D slots, D
-// planes ahead of the consumer.  CTA = (BY + 2) warps: warp w stands for lattice row
-// q1 = y0 - 1 + w (warps 0 and BY + 1 are halo rows; they also compute rho of the tile's two
-// halo columns), lane l owns nodes q2 = x0 + 2 l, x0 + 2 l + 1 (BX = 64).  Per plane u, step A
-// pulls the lane's populations (kept in registers) and writes rho into one of three rotating rho
-// plane; step B collides plane u - 1: one barrier per plane.  Face rules are reads of other
-// staged values (bounce-back / anti-bounce-back: the node's own opposite population; free:
-// the node's own population).  Nodes whose rule reaches outside the staged boxes (a halo row
-// on a face, a halo column on a q2 face, the first plane below the segment) pull from global
-// memory.  Every mbarrier wait is bounded: on expiry the CTA raises counters[3] and stops.
+// Raw post-collision planes are staged in shared memory by the Tensor Memory Accelerator and
+// consumed plane by plane along q3 (see step_tma_kernel).
 
-constexpr int kTmaBX = 64;
 constexpr long long kWaitLimit = 1LL << 20;  // x up to 2 us per try: about 2 s
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -151,11 +164,11 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
         "r"(bar) : "memory");
 }
 
-template <int BY>
+template <int BY, int BX>
 struct TmaLayout {
   // per population: main box (BY+2) x BX, left / right halo boxes (BY+2) x V, 128-B aligned
   template <typename S>
-  __host__ __device__ static constexpr int main_bytes() { return (BY + 2) * kTmaBX * (int)sizeof(S); }
+  __host__ __device__ static constexpr int main_bytes() { return (BY + 2) * BX * (int)sizeof(S); }
   __host__ __device__ static constexpr int halo_bytes() { return (((BY + 2) * 16) + 127) / 128 * 128; }
   template <typename S>
   __host__ __device__ static constexpr int pop_bytes() { return main_bytes<S>() + 2 * halo_bytes(); }
@@ -179,15 +192,12 @@ __device__ __forceinline__ bool named_sync_or(int id, int threads, bool v) {
       : "=r"(r) : "r"((unsigned)v), "r"(id), "r"(threads) : "memory");
   return r != 0;
 }
-template <typename T>
-__device__ __forceinline__ T lds(const unsigned char* base, int byte_off) {
-  return *reinterpret_cast<const T*>(base + byte_off);
-}
 
 // Fused step, TMA-staged.  CTA = BY + 2 consumer warps + 1 producer warp.  Consumer warp w
 // stands for lattice row q1 = y0 - 1 + w (warps 0 and BY + 1 are halo rows; they also compute
-// rho of the tile's two halo columns), lane l owns nodes q2 = x0 + 2 l, x0 + 2 l + 1
-// (BX = 64).  The producer's lane 0 stages raw plane p into slot (p - z0 + 2) mod NB: per
+// rho of the tile's two halo columns), lane l owns the NPT nodes q2 = x0 + NPT l ...
+// (BX = 32 NPT columns).  The producer's lane 0 stages raw plane p into slot
+// (p - z0 + 2) mod NB: per
 // population a main box of BX columns x BY + 2 rows (rows shifted by the population's xi1, so
 // the pull of tile row w reads staged row w of every population) and two V-column halo
 // boxes at x0 - V and x0 + BX (periodic wraps in the coordinates), plus the tile's
@@ -202,19 +212,20 @@ __device__ __forceinline__ T lds(const unsigned char* base, int byte_off) {
 // keeps halo rows off the q1 faces and halo columns off the q2 faces.  Shared memory is
 // addressed by 32-bit offsets from the dynamic array.  Every mbarrier wait is bounded: on
 // expiry counters[3] is raised and the CTA stops.
-template <typename S, int BY>
+template <typename S, int BY, int NPT>
 __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     const StepArgs<S> a, const __grid_constant__ CUtensorMap tm_main,
     const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_tab) {
   using R = typename Store<S>::R;
-  constexpr int NPT = 2, BX = kTmaBX, NB = 5, ROWS = BY + 2, NCW = ROWS;  // consumer warps
+  constexpr int BX = 32 * NPT, NB = 5, ROWS = BY + 2, NCW = ROWS;  // consumer warps
   constexpr int ES = (int)sizeof(S), RS = (int)sizeof(R);
   constexpr int V = 16 / ES;
-  constexpr int MB = TmaLayout<BY>::template main_bytes<S>();
-  constexpr int HB = TmaLayout<BY>::halo_bytes();
-  constexpr int POPB = TmaLayout<BY>::template pop_bytes<S>();
-  constexpr int SLOTB = TmaLayout<BY>::template slot_bytes<S>();
-  constexpr int PW = BX + 4;  // rho row: halo columns at 1 and BX + 2, nodes at 2 .. BX + 1
+  constexpr int MB = TmaLayout<BY, BX>::template main_bytes<S>();
+  constexpr int HB = TmaLayout<BY, BX>::halo_bytes();
+  constexpr int POPB = TmaLayout<BY, BX>::template pop_bytes<S>();
+  constexpr int SLOTB = TmaLayout<BY, BX>::template slot_bytes<S>();
+  // rho row: nodes at NPT .. NPT + BX - 1 (vector aligned), halo columns at NPT - 1, NPT + BX
+  constexpr int C0 = NPT, PW = BX + 2 * NPT;
   constexpr int PS = ROWS * PW;
   constexpr int TABB = ((BY * T_SLOTS * RS) + 127) / 128 * 128;
   constexpr int RHOB = ((3 * PS * RS) + 127) / 128 * 128;  // three rho planes
@@ -323,7 +334,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     const R sc0 = Store<S>::kScaled ? a.w[0] : R(1), sc1 = Store<S>::kScaled ? a.w[1] : R(1);
     auto wall = [&](int b) -> R { return b == LBW_BC_BOUNCE ? a.damping : R(-1); };
     auto ld1 = [&](unsigned off) -> R { return Store<S>::ld_smem(reinterpret_cast<const S*>(smem_raw + off)); };
-    auto ldv = [&](unsigned off, R (&o)[NPT]) { Vec<S>::ld(reinterpret_cast<const S*>(smem_raw + off), o); };
+    auto ldv = [&](unsigned off, R (&o)[NPT]) { VecN<S, NPT>::ld(reinterpret_cast<const S*>(smem_raw + off), o); };
     auto ldr = [&](unsigned off) -> R { return *reinterpret_cast<const R*>(smem_raw + off); };
 
     // offsets within a slot of this lane's vectors: pops 0, 3, 4, 5, 6 at (w, c0); pops 1 / 2
@@ -341,10 +352,10 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       if (b == LBW_BC_FREE) o2 = 2 * POPB + own - BX * ES;
       else { o2 = POPB + own + BX * ES; m2 = sc1 * wall(b); }
     }
-    // pop 3 of node c0 reads column c0 - 1 (left halo box for lane 0), pop 4 of node c0 + 1
-    // reads column c0 + 2 (right halo box for lane 31)
+    // pop 3 of node c0 reads column c0 - 1 (left halo box for lane 0), pop 4 of node
+    // c0 + NPT - 1 reads column c0 + NPT (right halo box for lane 31)
     const unsigned o3e = lane == 0 ? 3 * POPB + MB + w * 16 + (V - 1) * ES : 3 * POPB + own - ES;
-    const unsigned o4e = lane == 31 ? 4 * POPB + MB + HB + w * 16 : 4 * POPB + own + 2 * ES;
+    const unsigned o4e = lane == 31 ? 4 * POPB + MB + HB + w * 16 : 4 * POPB + own + NPT * ES;
     // q2 faces (non-periodic q2): free copies the node's own value, walls reflect the opposite
     const bool q2lo_free = a.bc[2] == LBW_BC_FREE, q2hi_free = a.bc[3] == LBW_BC_FREE;
     const R q2lo_m = sc1 * wall(a.bc[2]), q2hi_m = sc1 * wall(a.bc[3]);
@@ -385,8 +396,8 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
         else { h2 = hat(1, hw + 1); hm2 = sc1 * wall(b); }
       }
     }
-    const unsigned hrho = (unsigned)(((hl + 1) * PW + ((w == 0) ? 1 : BX + 2)) * RS);
-    const unsigned myrho = (unsigned)((w * PW + 2 + c0) * RS);
+    const unsigned hrho = (unsigned)(((hl + 1) * PW + ((w == 0) ? C0 - 1 : C0 + BX)) * RS);
+    const unsigned myrho = (unsigned)((w * PW + C0 + c0) * RS);
 
     // probes of this warp's row (recorded while the sample counter is below capacity)
     bool has_probe = false;
@@ -415,9 +426,12 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       ldv(B5 + own, f[5]);
       ldv(B6 + own, f[6]);
       f[3][0] = sc1 * ld1(S0 + o3e);
-      f[3][1] = sc1 * t3[0];
-      f[4][0] = sc1 * t4[1];
-      f[4][1] = sc1 * ld1(S0 + o4e);
+      f[4][NPT - 1] = sc1 * ld1(S0 + o4e);
+#pragma unroll
+      for (int k = 0; k + 1 < NPT; ++k) {
+        f[3][k + 1] = sc1 * t3[k];
+        f[4][k] = sc1 * t4[k + 1];
+      }
 #pragma unroll
       for (int k = 0; k < NPT; ++k) {
         if (Store<S>::kScaled) f[0][k] *= sc0;
@@ -425,7 +439,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       }
       if (!p2) {
         f[3][0] = q2lo ? (q2lo_free ? sc1 * t3[0] : q2lo_m * t4[0]) : f[3][0];
-        f[4][1] = q2hi ? (q2hi_free ? sc1 * t4[1] : q2hi_m * t3[1]) : f[4][1];
+        f[4][NPT - 1] = q2hi ? (q2hi_free ? sc1 * t4[NPT - 1] : q2hi_m * t3[NPT - 1]) : f[4][NPT - 1];
       }
       const bool ghost = zghost || !rowin;
 #pragma unroll
@@ -435,7 +449,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       }
       if (wr) {
         const unsigned pl = RHO + rbu * (PS * RS);
-        RVec<R>::st(reinterpret_cast<R*>(smem_raw + pl + myrho), rr);
+        VecN<R, NPT>::st(reinterpret_cast<R*>(smem_raw + pl + myrho), rr);
         if (hwarp) {
           R g[7];
           g[0] = sc0 * ld1(S0 + h0);
@@ -456,11 +470,17 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
                      const R (&rn)[NPT], int slz, int rbz) {
       const unsigned cur = RHO + rbz * (PS * RS) + myrho;
       R ru[NPT], rd[NPT];
-      RVec<R>::ld(reinterpret_cast<const R*>(smem_raw + cur + PW * RS), ru);
-      RVec<R>::ld(reinterpret_cast<const R*>(smem_raw + cur - PW * RS), rd);
-      const R lft = ldr(cur - RS), rgt = ldr(cur + 2 * RS);
-      const R rl[NPT] = {q2lo ? a.s2lo * rc[0] : lft, rc[0]};
-      const R rrt[NPT] = {rc[1], q2hi ? a.s2hi * rc[1] : rgt};
+      VecN<R, NPT>::ld(reinterpret_cast<const R*>(smem_raw + cur + PW * RS), ru);
+      VecN<R, NPT>::ld(reinterpret_cast<const R*>(smem_raw + cur - PW * RS), rd);
+      const R lft = ldr(cur - RS), rgt = ldr(cur + NPT * RS);
+      R rl[NPT], rrt[NPT];
+      rl[0] = q2lo ? a.s2lo * rc[0] : lft;
+      rrt[NPT - 1] = q2hi ? a.s2hi * rc[NPT - 1] : rgt;
+#pragma unroll
+      for (int k = 0; k + 1 < NPT; ++k) {
+        rl[k + 1] = rc[k];
+        rrt[k] = rc[k + 1];
+      }
       const unsigned T = TAB + slz * TABB + (w - 1) * (T_SLOTS * RS);
       R c[T_SLOTS];
 #pragma unroll
@@ -474,39 +494,86 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
           c[k] = v0.x; c[k + 1] = v0.y; c[k + 2] = v1.x; c[k + 3] = v1.y;
         }
       }
+      if constexpr (sizeof(R) == 4) {
+        // node pairs (k, k + 1) in paired FP32 instructions; negated coefficients give -D1 and
+        // -D3 directly
+        const float2 A1P = bc2(-c[T_A1P]), A1M = bc2(c[T_A1M]), C13P = bc2(-c[T_C13P]),
+                     C13M = bc2(c[T_C13M]), S1 = bc2(-c[T_S1]), B13P = bc2(-c[T_B13P]),
+                     B13M = bc2(c[T_B13M]), C33P = bc2(-c[T_C33P]), C33M = bc2(c[T_C33M]),
+                     S3 = bc2(-c[T_S3]), H22 = bc2(c[T_H22]), MG1 = bc2(c[T_MG1]),
+                     MG3 = bc2(c[T_MG3]), CS2 = bc2(a.cs2), W0 = bc2(a.two_w0), HALF = bc2(0.5f),
+                     MHALF = bc2(-0.5f);
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        const R rho = rc[k];
-        const R D1 = c[T_A1P] * ru[k] - c[T_A1M] * rd[k] + c[T_C13P] * rn[k] - c[T_C13M] * rp[k] +
-                     c[T_S1] * rho;
-        const R D3 = c[T_B13P] * ru[k] - c[T_B13M] * rd[k] + c[T_C33P] * rn[k] - c[T_C33M] * rp[k] +
-                     c[T_S3] * rho;
-        const R D2 = c[T_H22] * (rrt[k] - rl[k]);
-        const R j1 = (fc[1][k] - fc[2][k]) + R(0.5) * (c[T_MG1] * rho - D1);
-        const R j2 = (fc[3][k] - fc[4][k]) - R(0.5) * D2;
-        const R j3 = (fc[5][k] - fc[6][k]) + R(0.5) * (c[T_MG3] * rho - D3);
-        const R e = a.cs2 * rho;
-        fc[0][k] = a.two_w0 * rho - fc[0][k];
-        fc[1][k] = e + j1 - fc[1][k];
-        fc[2][k] = e - j1 - fc[2][k];
-        fc[3][k] = e + j2 - fc[3][k];
-        fc[4][k] = e - j2 - fc[4][k];
-        fc[5][k] = e + j3 - fc[5][k];
-        fc[6][k] = e - j3 - fc[6][k];
+        for (int k = 0; k < NPT; k += 2) {
+          const float2 rho = f2(rc[k], rc[k + 1]);
+          const float2 u = f2(ru[k], ru[k + 1]), d = f2(rd[k], rd[k + 1]);
+          const float2 n = f2(rn[k], rn[k + 1]), p = f2(rp[k], rp[k + 1]);
+          const float2 nD1 = fma2(S1, rho, fma2(C13M, p, fma2(C13P, n, fma2(A1M, d, mul2(A1P, u)))));
+          const float2 nD3 = fma2(S3, rho, fma2(C33M, p, fma2(C33P, n, fma2(B13M, d, mul2(B13P, u)))));
+          const float2 D2 = mul2(H22, sub2(f2(rrt[k], rrt[k + 1]), f2(rl[k], rl[k + 1])));
+          float2 F[7];
+#pragma unroll
+          for (int i = 0; i < 7; ++i) F[i] = f2(fc[i][k], fc[i][k + 1]);
+          const float2 j1 = fma2(HALF, fma2(MG1, rho, nD1), sub2(F[1], F[2]));
+          const float2 j2 = fma2(MHALF, D2, sub2(F[3], F[4]));
+          const float2 j3 = fma2(HALF, fma2(MG3, rho, nD3), sub2(F[5], F[6]));
+          const float2 e = mul2(CS2, rho);
+          float2 o[7];
+          o[0] = sub2(mul2(W0, rho), F[0]);
+          o[1] = sub2(add2(e, j1), F[1]);
+          o[2] = sub2(sub2(e, j1), F[2]);
+          o[3] = sub2(add2(e, j2), F[3]);
+          o[4] = sub2(sub2(e, j2), F[4]);
+          o[5] = sub2(add2(e, j3), F[5]);
+          o[6] = sub2(sub2(e, j3), F[6]);
+#pragma unroll
+          for (int i = 0; i < 7; ++i) {
+            fc[i][k] = o[i].x;
+            fc[i][k + 1] = o[i].y;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+          const R rho = rc[k];
+          const R D1 = c[T_A1P] * ru[k] - c[T_A1M] * rd[k] + c[T_C13P] * rn[k] - c[T_C13M] * rp[k] +
+                       c[T_S1] * rho;
+          const R D3 = c[T_B13P] * ru[k] - c[T_B13M] * rd[k] + c[T_C33P] * rn[k] - c[T_C33M] * rp[k] +
+                       c[T_S3] * rho;
+          const R D2 = c[T_H22] * (rrt[k] - rl[k]);
+          const R j1 = (fc[1][k] - fc[2][k]) + R(0.5) * (c[T_MG1] * rho - D1);
+          const R j2 = (fc[3][k] - fc[4][k]) - R(0.5) * D2;
+          const R j3 = (fc[5][k] - fc[6][k]) + R(0.5) * (c[T_MG3] * rho - D3);
+          const R e = a.cs2 * rho;
+          fc[0][k] = a.two_w0 * rho - fc[0][k];
+          fc[1][k] = e + j1 - fc[1][k];
+          fc[2][k] = e - j1 - fc[2][k];
+          fc[3][k] = e + j2 - fc[3][k];
+          fc[4][k] = e - j2 - fc[4][k];
+          fc[5][k] = e + j3 - fc[5][k];
+          fc[6][k] = e - j3 - fc[6][k];
+        }
       }
       S* dst = dst_z0 + (long long)(zc - z0) * n12;
 #pragma unroll
       for (int i = 0; i < 7; ++i) {
-        if (Store<S>::kScaled) { fc[i][0] *= a.inv_w[i]; fc[i][1] *= a.inv_w[i]; }
-        Vec<S>::st(dst, fc[i]);
+        if (Store<S>::kScaled) {
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) fc[i][k] *= a.inv_w[i];
+        }
+        VecN<S, NPT>::st(dst, fc[i]);
         dst += a.nn;
       }
       if (has_probe) {
         for (int s = 0; s < probe_cnt; ++s) {
           const int k = probe_list[s];
           const int dq = a.probe_q[3 * k + 1] - q2;
-          if (a.probe_q[3 * k] == q1 && dq >= 0 && dq < NPT && a.probe_q[3 * k + 2] == zc)
-            a.series[(long long)k * a.cap + t_sample] = (double)(dq == 0 ? rc[0] : rc[1]) * (double)c[T_INVSG];
+          if (a.probe_q[3 * k] == q1 && dq >= 0 && dq < NPT && a.probe_q[3 * k + 2] == zc) {
+            R v = rc[0];
+#pragma unroll
+            for (int j = 1; j < NPT; ++j) v = dq == j ? rc[j] : v;
+            a.series[(long long)k * a.cap + t_sample] = (double)v * (double)c[T_INVSG];
+          }
         }
       }
     };
@@ -609,14 +676,27 @@ StepArgs<S> make_args(Grid* g, int src) {
   return a;
 }
 
-template <typename S, int BY>
+template <typename S, int BY, int NPT>
 constexpr size_t tma_smem_bytes() {
   using R = typename Store<S>::R;
-  constexpr int NB = 5, PS = (BY + 2) * (kTmaBX + 4);
+  constexpr int BX = 32 * NPT, NB = 5, PS = (BY + 2) * (BX + 2 * NPT);
   constexpr int TABB = ((BY * T_SLOTS * (int)sizeof(R)) + 127) / 128 * 128;
   return 128 /* alignment slack */ + 128 /* barriers */ +
-         (size_t)NB * TmaLayout<BY>::template slot_bytes<S>() +
+         (size_t)NB * TmaLayout<BY, BX>::template slot_bytes<S>() +
          ((3 * PS * sizeof(R) + 127) / 128) * 128 + (size_t)NB * TABB;  // see step_tma_kernel
+}
+
+// The tile kernel for (rows BY, nodes per lane NPT): f(kernel, dynamic shared bytes).  Four
+// nodes per lane (128-column tiles) exist for the 16-bit storage formats only.
+template <typename S, typename F>
+auto tma_dispatch(int by, int npt, F&& f) {
+  if constexpr (sizeof(S) == 2) {
+    if (npt == 4)
+      return by == 7 ? f(step_tma_kernel<S, 7, 4>, tma_smem_bytes<S, 7, 4>())
+                     : f(step_tma_kernel<S, 4, 4>, tma_smem_bytes<S, 4, 4>());
+  }
+  return by == 7 ? f(step_tma_kernel<S, 7, 2>, tma_smem_bytes<S, 7, 2>())
+                 : f(step_tma_kernel<S, 4, 2>, tma_smem_bytes<S, 4, 2>());
 }
 
 template <typename S>
@@ -635,44 +715,47 @@ cudaError_t launch_step_t(Grid* g, int src) {
     cfg.stream = g->stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (g->tma_by == 7) {
-      cfg.dynamicSmemBytes = tma_smem_bytes<S, 7>();
-      return cudaLaunchKernelEx(&cfg, step_tma_kernel<S, 7>, a, m[2 * src], m[2 * src + 1], m[4]);
-    }
-    cfg.dynamicSmemBytes = tma_smem_bytes<S, 4>();
-    return cudaLaunchKernelEx(&cfg, step_tma_kernel<S, 4>, a, m[2 * src], m[2 * src + 1], m[4]);
-  } else {
-    dim3 block(g->bx, g->by);
-    size_t smem = 3 * (size_t)(g->bx + 2) * (g->by + 2) * sizeof(R);
-    step_kernel<S><<<g->grid_dim, block, smem, g->stream>>>(a);
+    return tma_dispatch<S>(g->tma_by, g->tma_npt, [&](auto kern, size_t smem) {
+      cfg.dynamicSmemBytes = smem;
+      return cudaLaunchKernelEx(&cfg, kern, a, m[2 * src], m[2 * src + 1], m[4]);
+    });
   }
+  dim3 block(g->bx, g->by);
+  size_t smem = 3 * (size_t)(g->bx + 2) * (g->by + 2) * sizeof(R);
+  step_kernel<S><<<g->grid_dim, block, smem, g->stream>>>(a);
   return cudaGetLastError();
 }
 
-template <typename S, int BY>
-int tma_regs_t() {
-  cudaFuncAttributes at;
-  if (cudaFuncGetAttributes(&at, step_tma_kernel<S, BY>) != cudaSuccess) {
-    cudaGetLastError();
-    return 255;
+struct TmaInfo {
+  int regs;
+  size_t smem;
+};
+
+template <typename S>
+TmaInfo tma_info_t(int by, int npt) {
+  return tma_dispatch<S>(by, npt, [&](auto kern, size_t smem) {
+    cudaFuncAttributes at;
+    int regs = 255;
+    if (cudaFuncGetAttributes(&at, kern) == cudaSuccess) regs = at.numRegs;
+    else cudaGetLastError();
+    return TmaInfo{regs, smem};
+  });
+}
+
+template <typename S>
+cudaError_t tma_prepare_t(int by, int npt) {
+  return tma_dispatch<S>(by, npt, [&](auto kern, size_t smem) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+}
+
+TmaInfo tma_info(int prec, int by, int npt) {
+  switch (prec) {
+    case LBW_F64: return tma_info_t<double>(by, npt);
+    case LBW_F32: return tma_info_t<float>(by, npt);
+    case LBW_F16S: return tma_info_t<__half>(by, npt);
+    default: return tma_info_t<__nv_bfloat16>(by, npt);
   }
-  return at.numRegs;
-}
-
-template <typename S>
-cudaError_t tma_prepare_t(int by) {
-  return by == 7 ? cudaFuncSetAttribute(step_tma_kernel<S, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)tma_smem_bytes<S, 7>())
-                 : cudaFuncSetAttribute(step_tma_kernel<S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)tma_smem_bytes<S, 4>());
-}
-
-template <typename S>
-void tma_candidates(int* regs, size_t* smem) {
-  regs[0] = tma_regs_t<S, 4>();
-  regs[1] = tma_regs_t<S, 7>();
-  smem[0] = tma_smem_bytes<S, 4>();
-  smem[1] = tma_smem_bytes<S, 7>();
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -681,8 +764,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapFloatOOBfill);
 
 // Tensor maps of the two population buffers (4-D: q2, q1, q3, population) with the main
-// (64 x BY+2) and halo (V x BY+2) boxes, and of the coefficient table (3-D: slot, q1, q3).
-bool build_tmaps(Grid* g, int by) {
+// (bx x BY+2) and halo (V x BY+2) boxes, and of the coefficient table (3-D: slot, q1, q3).
+bool build_tmaps(Grid* g, int by, int bx) {
   static EncodeTiledFn encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -703,7 +786,7 @@ bool build_tmaps(Grid* g, int by) {
   const cuuint64_t strides[3] = {(cuuint64_t)g->d.n[1] * es, (cuuint64_t)g->d.n[1] * g->d.n[0] * es,
                                  (cuuint64_t)g->nn * es};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const cuuint32_t box_main[4] = {(cuuint32_t)kTmaBX, (cuuint32_t)(by + 2), 1, 1};
+  const cuuint32_t box_main[4] = {(cuuint32_t)bx, (cuuint32_t)(by + 2), 1, 1};
   const cuuint32_t box_halo[4] = {(cuuint32_t)(16 / es), (cuuint32_t)(by + 2), 1, 1};
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(g->tmaps);
   for (int b = 0; b < 2; ++b) {
@@ -933,11 +1016,14 @@ cudaError_t launch_from_double(Grid* g, const double* d_f) {
                   [&](auto tag) { return launch_readout_t<decltype(tag)>(g, 2, nullptr, d_f); });
 }
 
-// Launch shape.  TMA tile kernel (q2 extent a multiple of 64, non-periodic q1): tile
-// 64 x BY with BY in {4, 7}; the resident CTAs per SM follow from shared memory and the
-// kernel's register count; the number of q3 segments minimises
-// waves x CTAs per SM x (planes per segment + 3) x (BY + 2), the bytes an SM moves with whole
-// waves counted.  Otherwise the register-pipelined kernel with 512-thread tiles.
+// Launch shape.  TMA tile kernel (q2 extent a multiple of the tile width, non-periodic q1):
+// tiles of BX = 64 columns (two nodes per lane) or, for 16-bit storage when the q2 extent is
+// a multiple of 128, BX = 128 (four nodes per lane: at 16-bit byte rates the two-node form
+// runs out of instruction issue); BY in {4, 7} rows, never with a halo row on the q1 = n1 - 1
+// face.  The resident CTAs per SM follow from shared memory and the kernel's register count;
+// the number of q3 segments minimises waves x CTAs per SM x (planes per segment + 3) x
+// (BY + 2) x BX, the node-planes an SM stages with whole waves counted.  Otherwise the
+// register-pipelined kernel with 512-thread tiles.
 void step_launch_shape(Grid* g) {
   const int n1 = g->d.n[0], n2 = g->d.n[1], n3 = g->d.n[2];
   int dev = 0, sms = 152, smem_max = 227 * 1024;
@@ -946,31 +1032,33 @@ void step_launch_shape(Grid* g) {
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   }
   g->tma_by = 0;
-  if (n2 % kTmaBX == 0 && g->d.bc[0] != LBW_BC_PERIODIC && g->nn * 7 < (1LL << 31)) {
-    int regs[2];
-    size_t smem[2];
-    switch (g->d.prec) {
-      case LBW_F64: tma_candidates<double>(regs, smem); break;
-      case LBW_F32: tma_candidates<float>(regs, smem); break;
-      case LBW_F16S: tma_candidates<__half>(regs, smem); break;
-      default: tma_candidates<__nv_bfloat16>(regs, smem);
-    }
+  const int npt = (g->elem == 2 && n2 % 128 == 0) ? 4 : 2, bx = 32 * npt;
+  if (n2 % bx == 0 && g->d.bc[0] != LBW_BC_PERIODIC && g->nn * 7 < (1LL << 31)) {
     const int bys[2] = {4, 7};
-    double best = 1e300;
+    int per_sm_of[2] = {0, 0};
     for (int c = 0; c < 2; ++c) {
       const int by = bys[c], threads = 32 * (by + 3);
-      if ((long long)smem[c] > smem_max || regs[c] > 255) continue;
+      const TmaInfo ti = tma_info(g->d.prec, by, npt);
+      if ((long long)ti.smem > smem_max || ti.regs > 255) continue;
       if ((n1 - 1) % by == 0) continue;  // a halo row would sit on the q1 = n1 - 1 face
-      const int rr = (regs[c] + 7) & ~7;
-      int per_sm = std::min<int>(2048 / threads, (int)((228LL * 1024) / (smem[c] + 1024)));
-      per_sm = std::max(1, std::min(per_sm, 65536 / (rr * threads)));
-      const long long tiles = (long long)(n2 / kTmaBX) * ((n1 + by - 1) / by);
+      const int rr = (ti.regs + 7) & ~7;
+      const int per_sm = std::min<int>(2048 / threads, (int)((228LL * 1024) / (ti.smem + 1024)));
+      per_sm_of[c] = std::max(1, std::min(per_sm, 65536 / (rr * threads)));
+    }
+    // a lone CTA per SM idles the SM at every plane barrier (measured: 16-bit trumpet 8% slower
+    // than two CTAs of fewer rows), so shapes with two or more resident CTAs come first
+    const bool two = per_sm_of[0] >= 2 || per_sm_of[1] >= 2;
+    double best = 1e300;
+    for (int c = 0; c < 2; ++c) {
+      const int by = bys[c], per_sm = per_sm_of[c];
+      if (per_sm == 0 || (two && per_sm < 2)) continue;
+      const long long tiles = (long long)(n2 / bx) * ((n1 + by - 1) / by);
       const long long slots = (long long)sms * per_sm;
       for (long long segs = 1; segs <= n3; ++segs) {
         const int lz = (int)((n3 + segs - 1) / segs);
         const long long blocks = tiles * ((n3 + lz - 1) / lz);
         const long long waves = (blocks + slots - 1) / slots;
-        const double cost = (double)waves * per_sm * (lz + 3) * (by + 2);
+        const double cost = (double)waves * per_sm * (lz + 3) * (by + 2) * bx;
         if (cost < best) {
           best = cost;
           g->tma_by = by;
@@ -979,25 +1067,26 @@ void step_launch_shape(Grid* g) {
       }
     }
     if (g->tma_by > 0) {
-      cudaError_t e = dispatch(g->d.prec, [&](auto tag) { return tma_prepare_t<decltype(tag)>(g->tma_by); });
-      if (e == cudaSuccess && build_tmaps(g, g->tma_by)) {
-        g->grid_dim = dim3(n2 / kTmaBX, (n1 + g->tma_by - 1) / g->tma_by, (n3 + g->lz - 1) / g->lz);
+      g->tma_npt = npt;
+      cudaError_t e = dispatch(g->d.prec, [&](auto tag) { return tma_prepare_t<decltype(tag)>(g->tma_by, npt); });
+      if (e == cudaSuccess && build_tmaps(g, g->tma_by, bx)) {
+        g->grid_dim = dim3(n2 / bx, (n1 + g->tma_by - 1) / g->tma_by, (n3 + g->lz - 1) / g->lz);
         return;
       }
       cudaGetLastError();
       g->tma_by = 0;
     }
   }
-  int bx = std::min(128, ((n2 + 31) / 32) * 32);
-  int by = 512 / bx;
-  g->bx = bx;
-  g->by = by;
-  const long long cols = (long long)((n2 + bx - 1) / bx) * ((n1 + by - 1) / by);
+  int bx2 = std::min(128, ((n2 + 31) / 32) * 32);
+  int by2 = 512 / bx2;
+  g->bx = bx2;
+  g->by = by2;
+  const long long cols = (long long)((n2 + bx2 - 1) / bx2) * ((n1 + by2 - 1) / by2);
   const long long slots = (long long)sms * 2;
   long long segs = std::max<long long>(1, slots / cols);
   segs = std::min<long long>(segs, n3);
   g->lz = (int)((n3 + segs - 1) / segs);
-  g->grid_dim = dim3((n2 + bx - 1) / bx, (n1 + by - 1) / by, (n3 + g->lz - 1) / g->lz);
+  g->grid_dim = dim3((n2 + bx2 - 1) / bx2, (n1 + by2 - 1) / by2, (n3 + g->lz - 1) / g->lz);
 }
 
 }  // namespace lbw

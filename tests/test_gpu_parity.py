@@ -51,6 +51,14 @@ SPECS = {
     "torus": GridSpec(kind=KIND_TOROIDAL, n=(13, 128, 24), h=(1, TWO_PI / 128, TWO_PI / 24),
                       x0=(4, 0, 0), c=0.4, geom=(40.0, 0, 0, 0),
                       bc=(BC_FREE, BC_BOUNCE, 0, 0, 0, 0)),
+    # tile kernel with every q2 face rule (two tiles of 64, or one of 128 for 16-bit storage)
+    "cartesian_tiled": GridSpec(kind=KIND_CARTESIAN, n=(9, 128, 11), h=(1, 1, 1), x0=(0, 0, 0),
+                                c=0.45, bc=(BC_FREE, BC_BOUNCE, BC_ANTIBOUNCE, BC_FREE,
+                                            BC_BOUNCE, BC_ANTIBOUNCE), damping=0.9),
+    # 16-bit storage: two 128-column tiles, q3 faces with anti-bounce-back and free ends
+    "cylinder_wide": GridSpec(kind=KIND_CYLINDRICAL, n=(21, 256, 17), h=(1, TWO_PI / 256, 1),
+                              x0=(26, 0, 0), c=0.4,
+                              bc=(BC_BOUNCE, BC_ANTIBOUNCE, 0, 0, BC_ANTIBOUNCE, BC_FREE)),
 }
 
 

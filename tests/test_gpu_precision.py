@@ -25,7 +25,8 @@ STEPS = 200
 
 
 @pytest.mark.parametrize("prec", [PREC_F16S, PREC_BF16S], ids=["f16", "bf16"])
-@pytest.mark.parametrize("name", ["cylinder", "torus", "trumpet_exp", "polar"])
+@pytest.mark.parametrize("name", ["cylinder", "torus", "trumpet_exp", "polar", "cartesian_tiled",
+                                  "cylinder_wide"])
 def test_sixteen_bit_field_error_bound(name, prec):
     spec = SPECS[name].with_(prec=prec)
     g, o, _, _ = _run_both(spec, STEPS, seed=31)
