@@ -331,7 +331,11 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     const int c0 = lane * NPT;
     const int q2 = x0 + c0;
     const bool q2lo = !p2 && q2 == 0, q2hi = !p2 && q2 + NPT - 1 == a.n2 - 1;
-    const R sc0 = Store<S>::kScaled ? a.w[0] : R(1), sc1 = Store<S>::kScaled ? a.w[1] : R(1);
+    // 16-bit formats store h_i = f_i / w_i and the step works on h directly (rho = w0 h0 +
+    // w1 (h1 + ... + h6), h* = 2 f^eq / w - h), so no per-population scaling; the face and
+    // wall factors are the same for f and h (all moving populations share w1)
+    constexpr bool SC = Store<S>::kScaled;
+    const R sc0 = R(1), sc1 = R(1);
     auto wall = [&](int b) -> R { return b == LBW_BC_BOUNCE ? a.damping : R(-1); };
     auto ld1 = [&](unsigned off) -> R { return Store<S>::ld_smem(reinterpret_cast<const S*>(smem_raw + off)); };
     auto ldv = [&](unsigned off, R (&o)[NPT]) { VecN<S, NPT>::ld(reinterpret_cast<const S*>(smem_raw + off), o); };
@@ -432,20 +436,41 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
         f[3][k + 1] = sc1 * t3[k];
         f[4][k] = sc1 * t4[k + 1];
       }
-#pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        if (Store<S>::kScaled) f[0][k] *= sc0;
-        f[1][k] *= m1; f[2][k] *= m2; f[5][k] *= m5; f[6][k] *= m6;
-      }
       if (!p2) {
         f[3][0] = q2lo ? (q2lo_free ? sc1 * t3[0] : q2lo_m * t4[0]) : f[3][0];
         f[4][NPT - 1] = q2hi ? (q2hi_free ? sc1 * t4[NPT - 1] : q2hi_m * t3[NPT - 1]) : f[4][NPT - 1];
       }
       const bool ghost = zghost || !rowin;
+      if constexpr (sizeof(R) == 4) {
+        const float2 W0S = bc2(a.w[0]), W1S = bc2(a.w[1]);
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        const R s = ((f[0][k] + f[1][k]) + (f[2][k] + f[3][k])) + ((f[4][k] + f[5][k]) + f[6][k]);
-        rr[k] = ghost ? R(0) : s;
+        for (int k = 0; k < NPT; k += 2) {
+          float2 F[7];
+#pragma unroll
+          for (int i = 0; i < 7; ++i) F[i] = f2(f[i][k], f[i][k + 1]);
+          F[1] = mul2(bc2(m1), F[1]);
+          F[2] = mul2(bc2(m2), F[2]);
+          F[5] = mul2(bc2(m5), F[5]);
+          F[6] = mul2(bc2(m6), F[6]);
+          f[1][k] = F[1].x; f[1][k + 1] = F[1].y;
+          f[2][k] = F[2].x; f[2][k + 1] = F[2].y;
+          f[5][k] = F[5].x; f[5][k + 1] = F[5].y;
+          f[6][k] = F[6].x; f[6][k + 1] = F[6].y;
+          float2 sum;
+          if constexpr (SC)
+            sum = fma2(W0S, F[0], mul2(W1S, add2(add2(add2(F[1], F[2]), add2(F[3], F[4])), add2(F[5], F[6]))));
+          else
+            sum = add2(add2(add2(F[0], F[1]), add2(F[2], F[3])), add2(add2(F[4], F[5]), F[6]));
+          rr[k] = ghost ? R(0) : sum.x;
+          rr[k + 1] = ghost ? R(0) : sum.y;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+          f[1][k] *= m1; f[2][k] *= m2; f[5][k] *= m5; f[6][k] *= m6;
+          const R sum = ((f[0][k] + f[1][k]) + (f[2][k] + f[3][k])) + ((f[4][k] + f[5][k]) + f[6][k]);
+          rr[k] = ghost ? R(0) : sum;
+        }
       }
       if (wr) {
         const unsigned pl = RHO + rbu * (PS * RS);
@@ -459,7 +484,8 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
           g[4] = sc1 * ld1(S0 + h4);
           g[5] = m5 * ld1(B5 + h0);  // h0 addresses population 0: B5 / B6 add their own
           g[6] = m6 * ld1(B6 + h0);
-          const R h = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+          const R h = SC ? a.w[0] * g[0] + a.w[1] * (((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]))
+                         : ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
           if (hcol) *reinterpret_cast<R*>(smem_raw + pl + hrho) = (hin && !zghost) ? h : R(0);
         }
       }
@@ -501,8 +527,8 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
                      C13M = bc2(c[T_C13M]), S1 = bc2(-c[T_S1]), B13P = bc2(-c[T_B13P]),
                      B13M = bc2(c[T_B13M]), C33P = bc2(-c[T_C33P]), C33M = bc2(c[T_C33M]),
                      S3 = bc2(-c[T_S3]), H22 = bc2(c[T_H22]), MG1 = bc2(c[T_MG1]),
-                     MG3 = bc2(c[T_MG3]), CS2 = bc2(a.cs2), W0 = bc2(a.two_w0), HALF = bc2(0.5f),
-                     MHALF = bc2(-0.5f);
+                     MG3 = bc2(c[T_MG3]), CS2 = bc2(a.cs2), W0 = bc2(a.two_w0),
+                     HALF = bc2(SC ? 1.f / a.cs2 : 0.5f), MHALF = bc2(SC ? -1.f / a.cs2 : -0.5f);
 #pragma unroll
         for (int k = 0; k < NPT; k += 2) {
           const float2 rho = f2(rc[k], rc[k + 1]);
@@ -514,12 +540,14 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
           float2 F[7];
 #pragma unroll
           for (int i = 0; i < 7; ++i) F[i] = f2(fc[i][k], fc[i][k + 1]);
+          // unscaled: j = m + F/2, f* = 2 f^eq - f with 2 f^eq = cs2 rho +- j (2 w0 rho at rest);
+          // scaled (h = f / w): J = 2 j / cs2, h* = 2 rho +- J - h
           const float2 j1 = fma2(HALF, fma2(MG1, rho, nD1), sub2(F[1], F[2]));
           const float2 j2 = fma2(MHALF, D2, sub2(F[3], F[4]));
           const float2 j3 = fma2(HALF, fma2(MG3, rho, nD3), sub2(F[5], F[6]));
-          const float2 e = mul2(CS2, rho);
+          const float2 e = SC ? add2(rho, rho) : mul2(CS2, rho);
           float2 o[7];
-          o[0] = sub2(mul2(W0, rho), F[0]);
+          o[0] = SC ? sub2(e, F[0]) : sub2(mul2(W0, rho), F[0]);
           o[1] = sub2(add2(e, j1), F[1]);
           o[2] = sub2(sub2(e, j1), F[2]);
           o[3] = sub2(add2(e, j2), F[3]);
@@ -557,10 +585,6 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       S* dst = dst_z0 + (long long)(zc - z0) * n12;
 #pragma unroll
       for (int i = 0; i < 7; ++i) {
-        if (Store<S>::kScaled) {
-#pragma unroll
-          for (int k = 0; k < NPT; ++k) fc[i][k] *= a.inv_w[i];
-        }
         VecN<S, NPT>::st(dst, fc[i]);
         dst += a.nn;
       }
