@@ -152,17 +152,134 @@ def cpu_baseline(spec, pulses, probes, budget_s=15.0):
                       f"({dt:.1f} s) of the FP64 C oracle, OpenMP over nodes"}
 
 
+ENSEMBLE_STEPS = 512
+
+
+def run_ensemble(args):
+    """The batched form: seeded trumpets of uneven sizes (r, theta in [32, 96], z in [128, 512])
+    advanced together by the persistent ensemble kernel (shape from the library's autotuner,
+    untimed), each benchmark step = the time steps plus every member's spectrum."""
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1705_01801_gb300 import lbw
+    prec = PREC_OVERRIDE if PREC_OVERRIDE is not None else W.PREC_F32
+    specs, _ = W.ensemble(args.members, seed=5, prec=prec)
+    nodes = sum(s.nodes for s in specs)
+    lbm_steps = args.lbm_steps if args.lbm_steps != LBM_STEPS else ENSEMBLE_STEPS
+    stream = torch.cuda.Stream()
+    sh = lbw.ctypes.c_void_p(stream.cuda_stream)
+    b = lbw.Batch(specs, stream=sh)
+    tune_report = b.tune(trial_steps=2).strip().splitlines()[-1]
+    exc = [W.ensemble_excitation(s) for s in specs]
+    pulses = [e[0] for e in exc]
+    probes_q = np.stack([e[1] for e in exc])
+
+    def device_step():
+        b.init(pulses)
+        b.set_probes(probes_q, lbm_steps)
+        stream.synchronize()
+        ev0, ev1, ev2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        ev0.record(stream)
+        b.step(lbm_steps)
+        ev1.record(stream)
+        f, a, cnt = b.spectrum(8)
+        ev2.record(stream)
+        ev2.synchronize()
+        return ev0.elapsed_time(ev2), ev0.elapsed_time(ev1)
+
+    for _ in range(args.warmup):
+        device_step()
+    torch.cuda.synchronize()
+    tot, stp = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            t, s_ = device_step()
+            tot.append(t)
+            stp.append(s_)
+    my_ms = max_over_ranks(sum(tot), device="cuda")
+    value = whole_job_mlups(nodes, lbm_steps * args.steps, ws, my_ms / 1e3)
+    elem = {W.PREC_F64: 8, W.PREC_F32: 4, W.PREC_F16S: 2, W.PREC_BF16S: 2}[prec]
+    kernel_ms = sum(stp) / (args.steps * lbm_steps)
+    achieved = nodes * 14 * elem / (kernel_ms / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+
+    # end to end through the C ABI with host buffers: pulses and probe nodes in, series and
+    # spectra out
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.init(pulses)
+        b.set_probes(probes_q, lbm_steps)
+        b.step(lbm_steps)
+        series = b.read_probes()
+        f, a, cnt = b.spectrum(8)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")
+    e2e_value = whole_job_mlups(nodes, lbm_steps * args.steps, ws, e2e_s)
+    h2d = sum(np.asarray(p).nbytes for p in pulses) + probes_q.astype(np.int32).nbytes
+    d2h = series.nbytes + 2 * 8 * 8 * len(specs)
+    b.close()
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    base = None
+    if not args.no_cpu_baseline and ws == 1:
+        base = cpu_baseline(specs[0], pulses[0], probes_q[0], budget_s=15.0)
+        base["sample"] = "member 0 of the ensemble: " + base["sample"]
+    M = 1
+    while M < 4 * lbm_steps:
+        M *= 2
+    launches = args.steps * (lbm_steps + len(specs) * (2 + int(math.log2(M)) + 5))
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": my_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {W.PREC_F64: "f64", W.PREC_F32: "f32", W.PREC_F16S: "f16 storage / f32 math",
+                  W.PREC_BF16S: "bf16 storage / f32 math"}[prec], "data": "synthetic",
+        "config": {"workload": f"ensemble of {len(specs)} seeded trumpets (r, theta in [32, 96], "
+                               f"z in [128, 512]), {lbm_steps} time steps + per-member spectrum "
+                               "per step, 8 probes per member",
+                   "nodes": nodes, "time_steps_per_step": lbm_steps, "shape": tune_report,
+                   "l2": f"working set {2 * 7 * nodes * elem / 1e9:.1f} GB vs 129 MB L2",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "ensemble step kernel",
+                     "peak_source": peak_kind, "bytes_per_node": 14 * elem,
+                     "kernel_us": kernel_ms * 1e3},
+        "cpu_baseline": base,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    wl = workload()
-    spec = wl.spec
+    if WORKLOAD == "ensemble":  # the oracle advances one member at a time: member 0
+        prec = PREC_OVERRIDE if PREC_OVERRIDE is not None else W.PREC_F32
+        spec = W.ensemble(args.members, seed=5, prec=prec)[0][0]
+        pulses_, probes_ = W.ensemble_excitation(spec)
+        label = f"ensemble member 0 ({args.members} seeded trumpets)"
+    else:
+        wl = workload()
+        spec, pulses_, probes_ = wl.spec, wl.pulses, wl.probes
+        label = WORKLOAD
     import oracle
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     g = oracle.OracleGrid(spec)
-    g.init(wl.pulses)
-    g.set_probes(wl.probes, 1 << 16)
+    g.init(pulses_)
+    g.set_probes(probes_, 1 << 16)
     g.step(1)
     t0 = time.perf_counter()
     g.step(1)
@@ -182,7 +299,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"cylinder {spec.n[0]}x{spec.n[1]}x{spec.n[2]}, "
+        "config": {"workload": f"{label} {spec.n[0]}x{spec.n[1]}x{spec.n[2]}, "
                                f"{per_step} time steps per benchmark step (bounded sample)",
                    "nodes": spec.nodes},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
@@ -203,7 +320,10 @@ def main():
     ap.add_argument("--lbm-steps", type=int, default=LBM_STEPS,
                     help="time steps per benchmark step (default: the workload's 20000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cylinder", choices=["cylinder", "disk", "trumpet", "torus"])
+    ap.add_argument("--workload", default="cylinder",
+                    choices=["cylinder", "disk", "trumpet", "torus", "ensemble"])
+    ap.add_argument("--members", type=int, default=512,
+                    help="ensemble members (--workload ensemble)")
     ap.add_argument("--vs-f64", action="store_true",
                     help="after the timed region, rerun the workload with FP64 storage on the "
                          "GPU and report the field and mode-frequency deviations")
@@ -217,6 +337,8 @@ def main():
                          "bf16s": W.PREC_BF16S}[args.prec]
     if args.impl == "reference":
         return run_reference(args)
+    if WORKLOAD == "ensemble":
+        return run_ensemble(args)
 
     import torch
     ws, rank, local = _dist()

@@ -34,7 +34,7 @@ def _stale(target, deps):
 def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = os.environ.get("NVCC", "nvcc")
     os.makedirs(os.path.join(OUT, "obj"), exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "lbw.h"))
     srcs = sources()
     objs = [os.path.join(OUT, "obj", os.path.basename(s) + ".o") for s in srcs]

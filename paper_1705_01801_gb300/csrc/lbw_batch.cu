@@ -20,6 +20,7 @@
 
 #include "lbw_internal.h"
 #include "lbw_march.cuh"
+#include "lbw_tma.cuh"
 
 namespace lbw {
 namespace {
@@ -59,8 +60,438 @@ __global__ void __launch_bounds__(512) batch_step_kernel(const StepArgs<S>* __re
   finish_step(counters, nprobe, cap, gridDim.x);
 }
 
+// ---------------------------------------------------------------- TMA-staged ensemble ------
+//
+// Members whose q2 axis is periodic are stored with padded rows: G = 16 / sizeof(S) ghost
+// columns on each side of the n2 data columns (ghost-left = the last G data columns,
+// ghost-right = the first G), the row rounded up to 16 bytes.  A 64-column tile's box
+// [x0, x0 + 64 + 2 G) in stored columns starts 16-byte aligned; past the row end it reads
+// zeros (outside the tensor, no memory traffic).  A tile therefore stages each population with
+// ONE tensor copy whatever n2 is (ragged last tiles and the periodic wrap included), and the
+// step writes the ghost copies of the G nodes next to the wrap.  The persistent CTA walks (member, q2 tile, q1 tile, q3 segment) items; per item it
+// copies the member's StepArgs into shared memory, re-initialises its mbarriers and runs the
+// same producer / consumer pipeline as the single-lattice tile kernel (lbw_step.cu:
+// step_tma_kernel), two nodes per lane.  Tiles start at q1 = -1 instead of 0 when
+// (n1 - 1) is a multiple of BY, so no halo row ever sits on a q1 face.
+constexpr int kTmaBatchBX = 64;
+
+template <typename S, int BY>
+struct BatchTmaLayout {
+  static constexpr int G = 16 / (int)sizeof(S);
+  static constexpr int RW = kTmaBatchBX + 2 * G;  // staged row: G | 64 data columns | G
+  static constexpr int POPB = (((BY + 2) * RW * (int)sizeof(S)) + 127) / 128 * 128;
+  static constexpr int SLOTB = 7 * POPB;
+};
+
+template <typename S, int BY>
+constexpr size_t batch_tma_smem() {
+  using R = typename Store<S>::R;
+  constexpr int NB = 5, PS = (BY + 2) * (kTmaBatchBX + 4);
+  constexpr int TABB = ((BY * T_SLOTS * (int)sizeof(R)) + 127) / 128 * 128;
+  return 128 + 128 + (size_t)NB * BatchTmaLayout<S, BY>::SLOTB + ((3 * PS * sizeof(R) + 127) / 128) * 128 +
+         (size_t)NB * TABB;
+}
+
+__device__ __forceinline__ void mbar_inval(unsigned bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+
+template <typename S, int BY>
+__global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
+    const StepArgs<S>* __restrict__ members, const CUtensorMap* __restrict__ maps, int src,
+    const int4* __restrict__ items, int n_items, int lz, unsigned long long* counters, int nprobe,
+    long long cap) {
+  using R = typename Store<S>::R;
+  using L = BatchTmaLayout<S, BY>;
+  constexpr int NPT = 2, BX = kTmaBatchBX, NB = 5, ROWS = BY + 2, NCW = ROWS;
+  constexpr int ES = (int)sizeof(S), RS = (int)sizeof(R);
+  constexpr int G = L::G, RW = L::RW, POPB = L::POPB, SLOTB = L::SLOTB;
+  constexpr int C0 = NPT, PW = BX + 2 * NPT, PS = ROWS * PW;
+  constexpr int TABB = ((BY * T_SLOTS * RS) + 127) / 128 * 128;
+  constexpr int RHOB = ((3 * PS * RS) + 127) / 128 * 128;
+  constexpr bool SC = Store<S>::kScaled;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) StepArgs<S> A;
+  __shared__ int probe_list[kMaxProbes];
+  __shared__ int probe_cnt;
+  __shared__ int abort_flag;
+  __shared__ unsigned long long t_sample;
+
+  const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane, nthr = 32 * (BY + 3);
+  const unsigned sbase = smem_u32(smem_raw);
+  const unsigned OFF = (128u - (sbase & 127u)) & 127u;
+  const unsigned SL = OFF + 128, RHO = SL + NB * SLOTB, TAB = RHO + RHOB;
+  auto full_at = [&](int k) { return sbase + OFF + 8u * k; };
+  auto empty_at = [&](int k) { return sbase + OFF + 8u * (NB + k); };
+  if (tid == 0) {
+    abort_flag = 0;
+    t_sample = counters[1];
+  }
+
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4 item = items[it];  // member, x0 (data column), y0 (may be -1), z0
+    {
+      const unsigned* from = reinterpret_cast<const unsigned*>(members + item.x);
+      unsigned* to = reinterpret_cast<unsigned*>(&A);
+      for (int k = tid; k < (int)(sizeof(StepArgs<S>) / 4); k += nthr) to[k] = from[k];
+    }
+    if (tid == 0) {
+      for (int k = 0; k < NB; ++k) {
+        if (it != (int)blockIdx.x) {  // the previous item left its phases behind
+          mbar_inval(full_at(k));
+          mbar_inval(empty_at(k));
+        }
+        mbar_init_count(full_at(k), 1);
+        mbar_init_count(empty_at(k), NCW);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+      probe_cnt = 0;
+    }
+    __syncthreads();
+    const int x0 = item.y, y0 = item.z, z0 = item.w;
+    const int z1 = min(z0 + lz, A.n3);
+    const bool p3 = A.bc[4] == LBW_BC_PERIODIC;
+    if (tid < A.nprobe) {
+      const int pq1 = A.probe_q[3 * tid], pq2 = A.probe_q[3 * tid + 1], pq3 = A.probe_q[3 * tid + 2];
+      if (pq1 >= y0 && pq1 < y0 + BY && pq2 >= x0 && pq2 < x0 + BX && pq3 >= z0 && pq3 < z1)
+        probe_list[atomicAdd(&probe_cnt, 1)] = tid;
+    }
+    __syncthreads();
+    const CUtensorMap* tm_f = maps + 3 * item.x + src;
+    const CUtensorMap* tm_t = maps + 3 * item.x + 2;
+
+    auto wait_bar = [&](unsigned bar, unsigned parity) -> bool {
+      long long n = 0;
+      while (!mbar_try_wait(bar, parity)) {
+        if (++n > kWaitLimit) {
+          abort_flag = 1;
+          A.counters[3] = 1;
+          return false;
+        }
+      }
+      return true;
+    };
+
+    if (w == ROWS) {  // ---------------------------------------------------------- producer
+      if (lane == 0) {
+        // the previous item's generic-proxy reads of the slots come before these copies
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const unsigned tx_pop = (unsigned)(ROWS * RW * ES);
+        int s = 0, use = 0, issued = z0 - 3;
+        for (int p = z0 - 2; p <= z1 + 1; ++p) {
+          if (use > 0 && !wait_bar(empty_at(s), (unsigned)((use - 1) & 1))) break;
+          const unsigned bar = full_at(s);
+          const unsigned base = sbase + SL + s * SLOTB;
+          const int pg = resolve(p, A.n3, p3);
+          if (pg < 0) {
+            mbar_expect_tx(bar, 0);
+          } else if (p == z0 - 2) {  // only population 5 of this plane streams into the segment
+            mbar_expect_tx(bar, tx_pop);
+            tma_load_4d(base + 5 * POPB, tm_f, x0, y0 - 1, pg, 5, bar);
+          } else {
+            const bool tab = p >= z0 && p < z1;
+            mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
+#pragma unroll 1
+            for (int i = 0; i < 7; ++i) tma_load_4d(base + i * POPB, tm_f, x0, y0 - 1 - xi1_of(i), pg, i, bar);
+            if (tab) tma_load_3d(sbase + TAB + s * TABB, tm_t, 0, y0, pg, bar);
+          }
+          issued = p;
+          if (++s == NB) { s = 0; ++use; }
+        }
+        for (int p = max(z0 - 2, issued - NB + 1); p <= issued; ++p) {
+          const int k = p - (z0 - 2);
+          wait_bar(full_at(k % NB), (unsigned)((k / NB) & 1));
+        }
+      }
+    } else {  // -------------------------------------------------------------------- consumers
+      const int q1 = y0 - 1 + w;
+      const bool interior = w >= 1 && w <= BY;
+      const bool rowin = q1 >= 0 && q1 < A.n1;
+      const bool owner = interior && rowin;
+      const int c0 = lane * NPT, q2 = x0 + c0;
+      const int n2 = A.n2;
+      auto wall = [&](int b) -> R { return b == LBW_BC_BOUNCE ? A.damping : R(-1); };
+      auto ld1 = [&](unsigned off) -> R { return Store<S>::ld_smem(reinterpret_cast<const S*>(smem_raw + off)); };
+      auto ldv = [&](unsigned off, R (&o)[NPT]) { VecN<S, NPT>::ld(reinterpret_cast<const S*>(smem_raw + off), o); };
+      auto ldr = [&](unsigned off) -> R { return *reinterpret_cast<const R*>(smem_raw + off); };
+
+      const unsigned own = (unsigned)((w * RW + G + c0) * ES);
+      unsigned o1 = POPB + own, o2 = 2 * POPB + own;
+      R m1 = R(1), m2 = R(1);
+      if (rowin && q1 == 0) {
+        const int b = A.bc[0];
+        if (b == LBW_BC_FREE) o1 = POPB + own + RW * ES;
+        else { o1 = 2 * POPB + own - RW * ES; m1 = wall(b); }
+      }
+      if (rowin && q1 == A.n1 - 1) {
+        const int b = A.bc[1];
+        if (b == LBW_BC_FREE) o2 = 2 * POPB + own - RW * ES;
+        else { o2 = POPB + own + RW * ES; m2 = wall(b); }
+      }
+      const unsigned o3e = 3 * POPB + own - ES, o4e = 4 * POPB + own + NPT * ES;
+      const unsigned f5_face = (A.bc[4] == LBW_BC_FREE ? 5 : 6) * POPB;
+      const unsigned f6_face = (A.bc[5] == LBW_BC_FREE ? 6 : 5) * POPB;
+      const R m5_face = A.bc[4] == LBW_BC_FREE ? R(1) : wall(A.bc[4]);
+      const R m6_face = A.bc[5] == LBW_BC_FREE ? R(1) : wall(A.bc[5]);
+
+      // halo column node of a halo warp: warp 0 lane l -> (y0 + l, x0 - 1), warp BY + 1 ->
+      // (y0 + l, x0 + BX), lanes l < BY; both live inside the staged rows (ghost columns)
+      const bool hwarp = !interior;
+      const int hl = lane < BY ? lane : BY - 1;
+      const int hq1 = y0 + hl;
+      const bool hcol = hwarp && lane < BY;
+      const bool hin = hq1 >= 0 && hq1 < A.n1;
+      unsigned h0, h1, h2, h3, h4;
+      R hm1 = R(1), hm2 = R(1);
+      {
+        const int hw = hl + 1, hc = (w == 0) ? G - 1 : G + BX;  // staged column of the node
+        auto hat = [&](int pop, int row, int col) { return (unsigned)(pop * POPB + (row * RW + col) * ES); };
+        h0 = hat(0, hw, hc);
+        h1 = hat(1, hw, hc);
+        h2 = hat(2, hw, hc);
+        h3 = hat(3, hw, hc - 1);
+        h4 = hat(4, hw, hc + 1);
+        if (hq1 == 0) {
+          const int b = A.bc[0];
+          if (b == LBW_BC_FREE) h1 = hat(1, hw + 1, hc);
+          else { h1 = hat(2, hw - 1, hc); hm1 = wall(b); }
+        }
+        if (hq1 == A.n1 - 1) {
+          const int b = A.bc[1];
+          if (b == LBW_BC_FREE) h2 = hat(2, hw - 1, hc);
+          else { h2 = hat(1, hw + 1, hc); hm2 = wall(b); }
+        }
+      }
+      const unsigned hrho = (unsigned)(((hl + 1) * PW + ((w == 0) ? C0 - 1 : C0 + BX)) * RS);
+      const unsigned myrho = (unsigned)((w * PW + C0 + c0) * RS);
+
+      bool has_probe = false;
+      if (owner && t_sample < (unsigned long long)A.cap)
+        for (int s = 0; s < probe_cnt; ++s) has_probe |= A.probe_q[3 * probe_list[s]] == q1;
+
+      R fA[7][NPT], fB[7][NPT], rA[NPT], rB[NPT], rC[NPT];
+      // storage of this lane's nodes (padded rows) and their ghost copies near the wrap
+      const long long row_stride = (long long)A.n1 * A.pitch;
+      S* const dst_z0 = A.fout + ((long long)z0 * A.n1 + (owner ? q1 : 0)) * A.pitch + G + q2;
+      const int nvalid = q2 + 1 < n2 ? 2 : (q2 < n2 ? 1 : 0);
+      const int gh0 = q2 < G ? n2 : (q2 >= n2 - G ? -n2 : 0);          // column shift of the
+      const int gh1 = q2 + 1 < G ? n2 : (q2 + 1 >= n2 - G ? -n2 : 0);  // ghost copy, 0: none
+
+      auto stepA = [&](int u, R (&f)[7][NPT], R (&rr)[NPT], int slm, int sl0, int slp, int rbu,
+                       bool wr) {
+        const bool zlo = !p3 && u == 0, zhi = !p3 && u == A.n3 - 1;
+        const bool zghost = !p3 && (u < 0 || u >= A.n3);
+        const unsigned S0 = SL + sl0 * SLOTB;
+        const unsigned B5 = zlo ? S0 + f5_face : SL + slm * SLOTB + 5 * POPB;
+        const unsigned B6 = zhi ? S0 + f6_face : SL + slp * SLOTB + 6 * POPB;
+        const R m5 = zlo ? m5_face : R(1), m6 = zhi ? m6_face : R(1);
+        R t3[NPT], t4[NPT];
+        ldv(S0 + own, f[0]);
+        ldv(S0 + o1, f[1]);
+        ldv(S0 + o2, f[2]);
+        ldv(S0 + 3 * POPB + own, t3);
+        ldv(S0 + 4 * POPB + own, t4);
+        ldv(B5 + own, f[5]);
+        ldv(B6 + own, f[6]);
+        f[3][0] = ld1(S0 + o3e);
+        f[3][1] = t3[0];
+        f[4][0] = t4[1];
+        f[4][1] = ld1(S0 + o4e);
+        const bool ghost = zghost || !rowin;
+        if constexpr (sizeof(R) == 4) {
+          float2 F[7];
+#pragma unroll
+          for (int i = 0; i < 7; ++i) F[i] = f2(f[i][0], f[i][1]);
+          F[1] = mul2(bc2(m1), F[1]);
+          F[2] = mul2(bc2(m2), F[2]);
+          F[5] = mul2(bc2(m5), F[5]);
+          F[6] = mul2(bc2(m6), F[6]);
+          f[1][0] = F[1].x; f[1][1] = F[1].y;
+          f[2][0] = F[2].x; f[2][1] = F[2].y;
+          f[5][0] = F[5].x; f[5][1] = F[5].y;
+          f[6][0] = F[6].x; f[6][1] = F[6].y;
+          float2 sum;
+          if constexpr (SC)
+            sum = fma2(bc2(A.w[0]), F[0],
+                       mul2(bc2(A.w[1]), add2(add2(add2(F[1], F[2]), add2(F[3], F[4])), add2(F[5], F[6]))));
+          else
+            sum = add2(add2(add2(F[0], F[1]), add2(F[2], F[3])), add2(add2(F[4], F[5]), F[6]));
+          rr[0] = ghost ? R(0) : sum.x;
+          rr[1] = ghost ? R(0) : sum.y;
+        } else {
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+            f[1][k] *= m1; f[2][k] *= m2; f[5][k] *= m5; f[6][k] *= m6;
+            const R sum = ((f[0][k] + f[1][k]) + (f[2][k] + f[3][k])) + ((f[4][k] + f[5][k]) + f[6][k]);
+            rr[k] = ghost ? R(0) : sum;
+          }
+        }
+        if (wr) {
+          const unsigned pl = RHO + rbu * (PS * RS);
+          VecN<R, NPT>::st(reinterpret_cast<R*>(smem_raw + pl + myrho), rr);
+          if (hwarp) {
+            R g[7];
+            g[0] = ld1(S0 + h0);
+            g[1] = hm1 * ld1(S0 + h1);
+            g[2] = hm2 * ld1(S0 + h2);
+            g[3] = ld1(S0 + h3);
+            g[4] = ld1(S0 + h4);
+            g[5] = m5 * ld1(B5 + h0);  // h0 addresses population 0: B5 / B6 add their own
+            g[6] = m6 * ld1(B6 + h0);
+            const R h = SC ? A.w[0] * g[0] + A.w[1] * (((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]))
+                           : ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+            if (hcol) *reinterpret_cast<R*>(smem_raw + pl + hrho) = (hin && !zghost) ? h : R(0);
+          }
+        }
+      };
+
+      auto stepB = [&](int zc, R (&fc)[7][NPT], const R (&rp)[NPT], const R (&rc)[NPT],
+                       const R (&rn)[NPT], int slz, int rbz) {
+        const unsigned cur = RHO + rbz * (PS * RS) + myrho;
+        R ru[NPT], rd[NPT];
+        VecN<R, NPT>::ld(reinterpret_cast<const R*>(smem_raw + cur + PW * RS), ru);
+        VecN<R, NPT>::ld(reinterpret_cast<const R*>(smem_raw + cur - PW * RS), rd);
+        const R rl[NPT] = {ldr(cur - RS), rc[0]};
+        const R rrt[NPT] = {rc[1], ldr(cur + NPT * RS)};
+        const unsigned T = TAB + slz * TABB + (w - 1) * (T_SLOTS * RS);
+        R c[T_SLOTS];
+#pragma unroll
+        for (int k = 0; k < T_SLOTS; k += 4) {
+          if (RS == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(smem_raw + T + k * RS);
+            c[k] = v.x; c[k + 1] = v.y; c[k + 2] = v.z; c[k + 3] = v.w;
+          } else {
+            const double2 v0 = *reinterpret_cast<const double2*>(smem_raw + T + k * RS);
+            const double2 v1 = *reinterpret_cast<const double2*>(smem_raw + T + (k + 2) * RS);
+            c[k] = v0.x; c[k + 1] = v0.y; c[k + 2] = v1.x; c[k + 3] = v1.y;
+          }
+        }
+        if constexpr (sizeof(R) == 4) {
+          const float2 A1P = bc2(-c[T_A1P]), A1M = bc2(c[T_A1M]), C13P = bc2(-c[T_C13P]),
+                       C13M = bc2(c[T_C13M]), S1 = bc2(-c[T_S1]), B13P = bc2(-c[T_B13P]),
+                       B13M = bc2(c[T_B13M]), C33P = bc2(-c[T_C33P]), C33M = bc2(c[T_C33M]),
+                       S3 = bc2(-c[T_S3]), H22 = bc2(c[T_H22]), MG1 = bc2(c[T_MG1]),
+                       MG3 = bc2(c[T_MG3]), CS2 = bc2(A.cs2), W0 = bc2(A.two_w0),
+                       HALF = bc2(SC ? 1.f / A.cs2 : 0.5f), MHALF = bc2(SC ? -1.f / A.cs2 : -0.5f);
+          const float2 rho = f2(rc[0], rc[1]);
+          const float2 u = f2(ru[0], ru[1]), d = f2(rd[0], rd[1]);
+          const float2 n = f2(rn[0], rn[1]), p = f2(rp[0], rp[1]);
+          const float2 nD1 = fma2(S1, rho, fma2(C13M, p, fma2(C13P, n, fma2(A1M, d, mul2(A1P, u)))));
+          const float2 nD3 = fma2(S3, rho, fma2(C33M, p, fma2(C33P, n, fma2(B13M, d, mul2(B13P, u)))));
+          const float2 D2 = mul2(H22, sub2(f2(rrt[0], rrt[1]), f2(rl[0], rl[1])));
+          float2 F[7];
+#pragma unroll
+          for (int i = 0; i < 7; ++i) F[i] = f2(fc[i][0], fc[i][1]);
+          const float2 j1 = fma2(HALF, fma2(MG1, rho, nD1), sub2(F[1], F[2]));
+          const float2 j2 = fma2(MHALF, D2, sub2(F[3], F[4]));
+          const float2 j3 = fma2(HALF, fma2(MG3, rho, nD3), sub2(F[5], F[6]));
+          const float2 e = SC ? add2(rho, rho) : mul2(CS2, rho);
+          float2 o[7];
+          o[0] = SC ? sub2(e, F[0]) : sub2(mul2(W0, rho), F[0]);
+          o[1] = sub2(add2(e, j1), F[1]);
+          o[2] = sub2(sub2(e, j1), F[2]);
+          o[3] = sub2(add2(e, j2), F[3]);
+          o[4] = sub2(sub2(e, j2), F[4]);
+          o[5] = sub2(add2(e, j3), F[5]);
+          o[6] = sub2(sub2(e, j3), F[6]);
+#pragma unroll
+          for (int i = 0; i < 7; ++i) {
+            fc[i][0] = o[i].x;
+            fc[i][1] = o[i].y;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+            const R rho = rc[k];
+            const R D1 = c[T_A1P] * ru[k] - c[T_A1M] * rd[k] + c[T_C13P] * rn[k] - c[T_C13M] * rp[k] +
+                         c[T_S1] * rho;
+            const R D3 = c[T_B13P] * ru[k] - c[T_B13M] * rd[k] + c[T_C33P] * rn[k] - c[T_C33M] * rp[k] +
+                         c[T_S3] * rho;
+            const R D2 = c[T_H22] * (rrt[k] - rl[k]);
+            const R j1 = (fc[1][k] - fc[2][k]) + R(0.5) * (c[T_MG1] * rho - D1);
+            const R j2 = (fc[3][k] - fc[4][k]) - R(0.5) * D2;
+            const R j3 = (fc[5][k] - fc[6][k]) + R(0.5) * (c[T_MG3] * rho - D3);
+            const R e = A.cs2 * rho;
+            fc[0][k] = A.two_w0 * rho - fc[0][k];
+            fc[1][k] = e + j1 - fc[1][k];
+            fc[2][k] = e - j1 - fc[2][k];
+            fc[3][k] = e + j2 - fc[3][k];
+            fc[4][k] = e - j2 - fc[4][k];
+            fc[5][k] = e + j3 - fc[5][k];
+            fc[6][k] = e - j3 - fc[6][k];
+          }
+        }
+        S* dst = dst_z0 + (long long)(zc - z0) * row_stride;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+          if (nvalid == 2) VecN<S, NPT>::st(dst, fc[i]);
+          else if (nvalid == 1) Store<S>::st(dst, fc[i][0]);
+          if (gh0 != 0 && nvalid >= 1) Store<S>::st(dst + gh0, fc[i][0]);
+          if (gh1 != 0 && nvalid == 2) Store<S>::st(dst + 1 + gh1, fc[i][1]);
+          dst += A.ps;
+        }
+        if (has_probe) {
+          for (int s = 0; s < probe_cnt; ++s) {
+            const int k = probe_list[s];
+            const int dq = A.probe_q[3 * k + 1] - q2;
+            if (A.probe_q[3 * k] == q1 && dq >= 0 && dq < NPT && A.probe_q[3 * k + 2] == zc)
+              A.series[(long long)k * A.cap + t_sample] = (double)(dq == 0 ? rc[0] : rc[1]) * (double)c[T_INVSG];
+          }
+        }
+      };
+
+      bool ok = wait_bar(full_at(0), 0) && wait_bar(full_at(1), 0) && wait_bar(full_at(2), 0);
+      if (ok && owner) stepA(z0 - 1, fB, rA, 0, 1, 2, 2, false);
+      if (lane == 0) mbar_arrive(empty_at(0));
+      ok = ok && wait_bar(full_at(3), 0);
+      if (ok) stepA(z0, fA, rB, 1, 2, 3, 0, true);
+      if (lane == 0) mbar_arrive(empty_at(1));
+      ok = !named_sync_or(1, NCW * 32, !ok || abort_flag);
+      int sz = 2, s1 = 3, s2 = 4, u2 = 0, rbz = 0, rb1 = 1;
+      auto advance = [&]() {
+        rbz = rb1;
+        rb1 = rb1 == 2 ? 0 : rb1 + 1;
+        sz = s1;
+        s1 = s2;
+        s2 = s2 == NB - 1 ? 0 : s2 + 1;
+        if (s2 == 0) ++u2;
+      };
+      auto iter = [&](int zz, R (&fc)[7][NPT], R (&fn)[7][NPT], const R (&rp)[NPT],
+                      const R (&rc)[NPT], R (&rn)[NPT], bool collide) {
+        const bool in = wait_bar(full_at(s2), (unsigned)(u2 & 1));
+        if (in) stepA(zz + 1, fn, rn, sz, s1, s2, rb1, true);
+        const bool go = !named_sync_or(1, NCW * 32, !in || abort_flag);
+        if (go && collide) stepB(zz, fc, rp, rc, rn, sz, rbz);
+        if (lane == 0) mbar_arrive(empty_at(sz));
+        advance();
+        return go;
+      };
+      int z = z0;
+      if (!owner) {
+        for (; ok && z < z1; ++z) ok = iter(z, fA, fB, rA, rB, rC, false);
+      } else {
+        for (; ok && z + 1 < z1; z += 2) {
+          ok = iter(z, fA, fB, rA, rB, rC, true);
+          if (!ok) break;
+          ok = iter(z + 1, fB, fA, rB, rC, rA, true);
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+            const R t = rA[k];
+            rA[k] = rC[k];
+            rB[k] = t;
+          }
+        }
+        if (ok && z < z1) ok = iter(z, fA, fB, rA, rB, rC, true);
+      }
+    }
+    __syncthreads();  // item done: the producer has drained, the next item re-uses everything
+    if (abort_flag) break;
+  }
+  finish_step(counters, nprobe, cap, gridDim.x);
+}
+
 struct Shape {
-  int by = 8;    // tile rows (CTA = 32 x by threads)
+  int by = 8;    // tile rows (register-pipelined: CTA = 32 x by threads; TMA: 4 or 7)
   int lz = 32;   // planes per q3 segment
   int cps = 2;   // CTAs per SM of the persistent grid
 };
@@ -92,6 +523,8 @@ struct lbw_batch {
   int64_t steps = 0;
   bool initialised = false;
   long long total_nodes = 0;
+  bool tma = false;              // padded members on the TMA-staged kernel
+  void* maps = nullptr;          // device: per member tensor maps (buffer 0, buffer 1, table)
 };
 
 namespace {
@@ -136,6 +569,9 @@ void fill_args(lbw_batch* b, int m, int src, StepArgs<S>& a) {
   a.cap = b->cap;
   a.counters = b->counters;
   a.nblocks = 0;
+  a.pitch = g.pitch ? g.pitch : g.d.n[1];
+  a.col0 = g.col0;
+  a.ps = pop_stride(&g);
 }
 
 template <typename S>
@@ -160,15 +596,89 @@ int max_cps() {
   return std::max(1, per);
 }
 
+// The TMA-staged kernel for (storage type, tile rows): f(kernel, dynamic shared bytes).
+template <typename S, typename F>
+auto batch_tma_dispatch(int by, F&& f) {
+  return by == 7 ? f(batch_tma_kernel<S, 7>, batch_tma_smem<S, 7>())
+                 : f(batch_tma_kernel<S, 4>, batch_tma_smem<S, 4>());
+}
+
+template <typename F>
+auto prec_dispatch(int prec, F&& f) {
+  switch (prec) {
+    case LBW_F64: return f(double());
+    case LBW_F32: return f(float());
+    case LBW_F16S: return f(__half());
+    default: return f(__nv_bfloat16());
+  }
+}
+
+// resident CTAs per SM of the TMA-staged kernel with `by` rows (0 when it cannot run)
+int tma_cps(int prec, int by) {
+  return prec_dispatch(prec, [&](auto tag) {
+    using S = decltype(tag);
+    return batch_tma_dispatch<S>(by, [&](auto kern, size_t smem) {
+      int per = 0;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * (by + 3), smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return per;
+    });
+  });
+}
+
+// Ghost columns of a padded member row and the row length (elements) for storage size es:
+// G | n2 data | G, rounded up to 16 bytes.  The last tile's box may reach past the row end;
+// those columns are outside the tensor and arrive as zeros without touching memory.
+int ghost_cols(size_t es) { return (int)(16 / es); }
+int padded_pitch(int n2, size_t es) {
+  const int v = (int)(16 / es);
+  return (n2 + 2 * ghost_cols(es) + v - 1) / v * v;
+}
+
+// Tensor maps of every member for tile rows `by`: 4-D views (stored column, q1, q3,
+// population) of both buffers with (64 + 2 G) x (by + 2) boxes, 3-D view of the table.
+lbw_status build_batch_maps(lbw_batch* b, int by) {
+  const size_t es = es_of(b->prec);
+  const int rprec = b->prec == LBW_F64 ? LBW_F64 : LBW_F32;
+  const size_t rs = rs_of(b->prec);
+  std::vector<CUtensorMap> h(3 * (size_t)b->n);
+  for (int m = 0; m < b->n; ++m) {
+    const Grid& g = b->views[m];
+    const uint64_t P = (uint64_t)g.pitch, n1 = (uint64_t)g.d.n[0], n3 = (uint64_t)g.d.n[2];
+    const uint64_t dims[4] = {P, n1, n3, 7};
+    const uint64_t strides[3] = {P * es, P * n1 * es, P * n1 * n3 * es};
+    const uint32_t box[4] = {(uint32_t)(kTmaBatchBX + 2 * g.col0), (uint32_t)(by + 2), 1, 1};
+    for (int k = 0; k < 2; ++k)
+      if (!encode_tiled_map(&h[3 * m + k], b->prec, 4, g.f[k], dims, strides, box))
+        return fail(LBW_ECUDA, "tensor map of ensemble member " + std::to_string(m));
+    const uint64_t tdims[3] = {(uint64_t)T_SLOTS, n1, n3};
+    const uint64_t tstr[2] = {(uint64_t)T_SLOTS * rs, (uint64_t)T_SLOTS * rs * n1};
+    const uint32_t tbox[3] = {(uint32_t)T_SLOTS, (uint32_t)by, 1};
+    if (!encode_tiled_map(&h[3 * m + 2], rprec, 3, g.table, tdims, tstr, tbox))
+      return fail(LBW_ECUDA, "table tensor map of ensemble member " + std::to_string(m));
+  }
+  if (!b->maps) LBW_CUDA(cudaMallocAsync(&b->maps, sizeof(CUtensorMap) * h.size(), b->stream));
+  LBW_CUDA(cudaMemcpyAsync(b->maps, h.data(), sizeof(CUtensorMap) * h.size(), cudaMemcpyHostToDevice,
+                           b->stream));
+  LBW_CUDA(cudaStreamSynchronize(b->stream));  // h is released on return
+  return LBW_OK;
+}
+
 // work list for the current shape: items of each member in (q3 segment, q1 tile, q2 tile)
-// order, so consecutive CTAs hold spatial neighbours
+// order, so consecutive CTAs hold spatial neighbours.  TMA tiles are 64 columns wide and
+// start at q1 = -1 when (n1 - 1) is a multiple of the tile rows (no halo row on a face).
 lbw_status build_items(lbw_batch* b) {
   std::vector<int4> items;
   for (int m = 0; m < b->n; ++m) {
     const lbw_grid_desc& d = b->views[m].d;
+    const int bx = b->tma ? kTmaBatchBX : kBatchBX;
+    const int y_start = (b->tma && (d.n[0] - 1) % b->shape.by == 0) ? -1 : 0;
     for (int z0 = 0; z0 < d.n[2]; z0 += b->shape.lz)
-      for (int y0 = 0; y0 < d.n[0]; y0 += b->shape.by)
-        for (int x0 = 0; x0 < d.n[1]; x0 += kBatchBX) items.push_back(make_int4(m, x0, y0, z0));
+      for (int y0 = y_start; y0 < d.n[0]; y0 += b->shape.by)
+        for (int x0 = 0; x0 < d.n[1]; x0 += bx) items.push_back(make_int4(m, x0, y0, z0));
   }
   if (b->items) cudaFreeAsync(b->items, b->stream);
   b->items = nullptr;
@@ -186,6 +696,10 @@ lbw_status build_items(lbw_batch* b) {
 lbw_status refresh(lbw_batch* b) {
   lbw_status st = build_items(b);
   if (st != LBW_OK) return st;
+  if (b->tma) {
+    st = build_batch_maps(b, b->shape.by);
+    if (st != LBW_OK) return st;
+  }
   switch (b->prec) {
     case LBW_F64: return upload_args<double>(b);
     case LBW_F32: return upload_args<float>(b);
@@ -197,6 +711,14 @@ lbw_status refresh(lbw_batch* b) {
 template <typename S>
 cudaError_t launch_batch_t(lbw_batch* b, int src) {
   using R = typename Store<S>::R;
+  if (b->tma) {
+    return batch_tma_dispatch<S>(b->shape.by, [&](auto kern, size_t smem) {
+      kern<<<b->blocks, dim3(32, b->shape.by + 3), smem, b->stream>>>(
+          reinterpret_cast<const StepArgs<S>*>(b->members[src]), reinterpret_cast<const CUtensorMap*>(b->maps),
+          src, b->items, b->n_items, b->shape.lz, b->counters, b->nprobe, b->cap);
+      return cudaGetLastError();
+    });
+  }
   const dim3 block(kBatchBX, b->shape.by);
   const size_t smem = 3 * (size_t)(kBatchBX + 2) * (b->shape.by + 2) * sizeof(R);
   batch_step_kernel<S><<<b->blocks, block, smem, b->stream>>>(
@@ -265,7 +787,8 @@ std::string signature(const lbw_batch* b) {
       h *= 1099511628211ULL;
     }
   std::ostringstream s;
-  s << "n" << b->n << "-p" << b->prec << "-nodes" << b->total_nodes << "-h" << std::hex << h;
+  s << "n" << b->n << "-p" << b->prec << (b->tma ? "-tma" : "-reg") << "-nodes" << b->total_nodes << "-h"
+    << std::hex << h;
   return s.str();
 }
 
@@ -297,6 +820,19 @@ lbw_status lbw_batch_create(const lbw_grid_desc* descs, int32_t n, void* stream,
   b->views.resize(n);
   b->foff.resize(n);
   b->toff.resize(n);
+  // the TMA-staged kernel takes ensembles whose members all wrap in q2 (ghost columns), have
+  // walls in q1, at least 2 G columns and 32-bit population offsets
+  {
+    const size_t es = es_of(b->prec);
+    b->tma = tma_cps(b->prec, 7) > 0 && tma_cps(b->prec, 4) > 0;
+    for (int m = 0; m < n && b->tma; ++m) {
+      const lbw_grid_desc& d = descs[m];
+      const long long ps = (long long)d.n[0] * d.n[2] * padded_pitch(d.n[1], es);
+      if (d.bc[2] != LBW_BC_PERIODIC || d.bc[3] != LBW_BC_PERIODIC || d.bc[0] == LBW_BC_PERIODIC ||
+          d.n[1] < 2 * ghost_cols(es) || 7 * ps >= (1LL << 31) || d.n[0] < 2)
+        b->tma = false;
+    }
+  }
   std::vector<double> tab_all;
   size_t ftot = 0;
   for (int m = 0; m < n; ++m) {
@@ -314,10 +850,14 @@ lbw_status lbw_batch_create(const lbw_grid_desc* descs, int32_t n, void* stream,
     g.elem = es_of(d.prec);
     g.w0 = 1.0 - 3.0 * d.cs2;
     g.w1 = 0.5 * d.cs2;
+    if (b->tma) {
+      g.pitch = padded_pitch(d.n[1], g.elem);
+      g.col0 = ghost_cols(g.elem);
+    }
     b->foff[m] = ftot;
     // 256-byte aligned member slices
     const size_t align = 256 / g.elem;
-    ftot += (7 * (size_t)g.nn + align - 1) / align * align;
+    ftot += (7 * (size_t)pop_stride(&g) + align - 1) / align * align;
     b->toff[m] = tab_all.size();
     tab_all.insert(tab_all.end(), tab.begin(), tab.end());
     while (tab_all.size() % 64) tab_all.push_back(0.0);
@@ -355,7 +895,12 @@ lbw_status lbw_batch_create(const lbw_grid_desc* descs, int32_t n, void* stream,
     g.table = static_cast<unsigned char*>(b->table) + b->toff[m] * rs;
     g.counters = b->counters;
   }
-  b->shape.cps = std::min(2, b->prec == LBW_F32 ? max_cps<float>() : 2);
+  if (b->tma) {
+    b->shape.by = 7;
+    b->shape.cps = std::min(2, tma_cps(b->prec, 7));
+  } else {
+    b->shape.cps = std::min(2, b->prec == LBW_F32 ? max_cps<float>() : 2);
+  }
   lbw_status st = refresh(b);
   if (st != LBW_OK) return cleanup(st);
   LBW_CUDA(cudaStreamSynchronize(b->stream));
@@ -373,6 +918,7 @@ void lbw_batch_destroy(lbw_batch* b) {
   if (b->table) cudaFreeAsync(b->table, b->stream);
   if (b->counters) cudaFreeAsync(b->counters, b->stream);
   if (b->items) cudaFreeAsync(b->items, b->stream);
+  if (b->maps) cudaFreeAsync(b->maps, b->stream);
   if (b->probe_q) cudaFreeAsync(b->probe_q, b->stream);
   if (b->series) cudaFreeAsync(b->series, b->stream);
   cudaStreamSynchronize(b->stream);
@@ -524,14 +1070,18 @@ lbw_status lbw_batch_tune(lbw_batch* b, int32_t trial_steps, const char* cache_p
   double best_ms = -1.0;
   std::ostringstream rep;
   if (!cached) {
-    const int cps_max = b->prec == LBW_F32 ? max_cps<float>() : 2;
-    const int bys[3] = {4, 8, 16}, lzs[3] = {16, 32, 64}, cpss[3] = {1, 2, 4};
+    // register-pipelined kernel: rows {4, 8, 16} x CTAs per SM {1, 2, 4}; TMA-staged kernel:
+    // rows {4, 7} x CTAs per SM {1, 2}; both x segment planes {16, 32, 64}
+    std::vector<int> bys = b->tma ? std::vector<int>{4, 7} : std::vector<int>{4, 8, 16};
+    std::vector<int> cpss = b->tma ? std::vector<int>{1, 2} : std::vector<int>{1, 2, 4};
+    const int lzs[3] = {16, 32, 64};
     cudaEvent_t e0, e1;
     LBW_CUDA(cudaEventCreate(&e0));
     LBW_CUDA(cudaEventCreate(&e1));
     for (int by : bys)
       for (int lz : lzs)
         for (int cps : cpss) {
+          const int cps_max = b->tma ? tma_cps(b->prec, by) : (b->prec == LBW_F32 ? max_cps<float>() : 2);
           if (cps > cps_max) continue;
           b->shape = Shape{by, lz, cps};
           lbw_status st = refresh(b);

@@ -50,6 +50,9 @@ struct Grid {
   int bx = 0, by = 0, lz = 0;
   int tma_by = 0;          // 0: register-pipelined kernel; 4 or 7: TMA tile kernel rows
   int tma_npt = 2;         // TMA tile kernel: nodes per lane (tile width 32 x tma_npt)
+  // padded storage (ensembles on the tile kernel): row length and first data column in
+  // elements; pitch 0 means dense rows of n2 values
+  int pitch = 0, col0 = 0;
   alignas(64) unsigned char tmaps[5 * 128];  // tensor maps: f[0] main/halo, f[1] main/halo, table
   dim3 grid_dim;
   // captured step chains, one per parity of the starting buffer
@@ -74,6 +77,11 @@ lbw_status cuda_fail(cudaError_t e, const char* what);
 lbw_status validate_desc(lbw_grid_desc& d);
 lbw_status build_force_table(const lbw_grid_desc& d, std::vector<double>& tab);
 
+// population stride of a lattice's storage in elements
+inline long long pop_stride(const Grid* g) {
+  return g->pitch ? (long long)g->d.n[0] * g->d.n[2] * g->pitch : g->nn;
+}
+
 // kernels (lbw_step.cu) ---------------------------------------------------------------------
 cudaError_t launch_step(Grid* g, int src);             // one time step, buffer src -> 1-src
 cudaError_t launch_init(Grid* g, const double* d_pulses, int npulse);
@@ -81,6 +89,10 @@ cudaError_t launch_field(Grid* g, double* d_P);        // P of the current state
 cudaError_t launch_to_double(Grid* g, double* d_f);    // current populations -> doubles
 cudaError_t launch_from_double(Grid* g, const double* d_f);
 void step_launch_shape(Grid* g);                       // choose bx, by, lz, grid_dim
+// 128-byte CUtensorMap for a tiled TMA view: element type from lbw_prec, dims / box innermost
+// first, strides in bytes of dimensions 1 .. rank - 1; false when the driver refuses it
+bool encode_tiled_map(void* map, int prec, int rank, void* base, const uint64_t* dims,
+                      const uint64_t* strides, const uint32_t* box);
 
 // spectrum (lbw_spectrum.cu) ----------------------------------------------------------------
 lbw_status spectrum_device(const double* d_x, int64_t T, int32_t n_series, int32_t stride_series,

@@ -59,6 +59,11 @@ struct StepArgs {
   long long cap;
   unsigned long long* counters;
   unsigned int nblocks;
+  // storage geometry of the populations: row length, first data column and population stride
+  // in elements (dense lattices: n2, 0, nn; ensembles on the tile kernel pad every row with
+  // ghost columns that mirror the periodic wrap)
+  int pitch, col0;
+  long long ps;
 };
 
 __device__ __forceinline__ long long node(int q1, int q2, int q3, int n1, int n2) {

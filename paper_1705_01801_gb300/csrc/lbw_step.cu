@@ -23,6 +23,7 @@
 
 #include "lbw_internal.h"
 #include "lbw_march.cuh"
+#include "lbw_tma.cuh"
 
 namespace lbw {
 namespace {
@@ -48,121 +49,10 @@ __global__ void __launch_bounds__(512) step_kernel(const StepArgs<S> a) {
   finish_step(a.counters, a.nprobe, a.cap, a.nblocks);
 }
 
-__device__ __forceinline__ int xi1_of(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
-
-// N consecutive nodes along q2 per lane, moved as one vector: FP32 8 / 16 bytes, FP64 16
-// bytes, 16-bit formats 4 / 8 bytes (converted to and from FP32 in pairs).
-template <typename S, int N> struct VecN;
-template <> struct VecN<float, 2> {
-  __device__ static void ld(const float* p, float (&o)[2]) {
-    const float2 v = *reinterpret_cast<const float2*>(p);
-    o[0] = v.x; o[1] = v.y;
-  }
-  __device__ static void st(float* p, const float (&o)[2]) {
-    *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
-  }
-};
-template <> struct VecN<float, 4> {
-  __device__ static void ld(const float* p, float (&o)[4]) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-  }
-  __device__ static void st(float* p, const float (&o)[4]) {
-    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-  }
-};
-template <> struct VecN<double, 2> {
-  __device__ static void ld(const double* p, double (&o)[2]) {
-    const double2 v = *reinterpret_cast<const double2*>(p);
-    o[0] = v.x; o[1] = v.y;
-  }
-  __device__ static void st(double* p, const double (&o)[2]) {
-    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
-  }
-};
-// 16-bit pairs <-> float2
-__device__ __forceinline__ float2 to_f2(__half2 v) { return __half22float2(v); }
-__device__ __forceinline__ float2 to_f2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
-template <typename P> __device__ __forceinline__ P from_f2(float a, float b);
-template <> __device__ __forceinline__ __half2 from_f2<__half2>(float a, float b) { return __floats2half2_rn(a, b); }
-template <> __device__ __forceinline__ __nv_bfloat162 from_f2<__nv_bfloat162>(float a, float b) {
-  return __floats2bfloat162_rn(a, b);
-}
-template <typename S> struct Pair16;
-template <> struct Pair16<__half> { using T = __half2; };
-template <> struct Pair16<__nv_bfloat16> { using T = __nv_bfloat162; };
-template <typename S> struct Vec16 {
-  using P = typename Pair16<S>::T;
-  __device__ static void ld(const S* p, float (&o)[2]) {
-    const float2 a = to_f2(*reinterpret_cast<const P*>(p));
-    o[0] = a.x; o[1] = a.y;
-  }
-  __device__ static void st(S* p, const float (&o)[2]) {
-    *reinterpret_cast<P*>(p) = from_f2<P>(o[0], o[1]);
-  }
-  __device__ static void ld(const S* p, float (&o)[4]) {
-    const uint2 u = *reinterpret_cast<const uint2*>(p);
-    const float2 a = to_f2(*reinterpret_cast<const P*>(&u.x)), b = to_f2(*reinterpret_cast<const P*>(&u.y));
-    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-  }
-  __device__ static void st(S* p, const float (&o)[4]) {
-    const P a = from_f2<P>(o[0], o[1]), b = from_f2<P>(o[2], o[3]);
-    uint2 u;
-    u.x = *reinterpret_cast<const unsigned*>(&a);
-    u.y = *reinterpret_cast<const unsigned*>(&b);
-    *reinterpret_cast<uint2*>(p) = u;
-  }
-};
-template <int N> struct VecN<__half, N> : Vec16<__half> {};
-template <int N> struct VecN<__nv_bfloat16, N> : Vec16<__nv_bfloat16> {};
-
-// Paired FP32 arithmetic (one instruction for two lanes' values of a node pair), the same
-// IEEE round-to-nearest operations as the scalar forms.
-__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
-__device__ __forceinline__ float2 add2(float2 x, float2 y) { return __fadd2_rn(x, y); }
-__device__ __forceinline__ float2 mul2(float2 x, float2 y) { return __fmul2_rn(x, y); }
-__device__ __forceinline__ float2 fma2(float2 x, float2 y, float2 z) { return __ffma2_rn(x, y, z); }
-__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, bc2(-1.f), x); }
-
 // ---------------------------------------------------------------- TMA tile kernel -------
 //
 // Raw post-collision planes are staged in shared memory by the Tensor Memory Accelerator and
 // consumed plane by plane along q3 (see step_tma_kernel).
-
-constexpr long long kWaitLimit = 1LL << 20;  // x up to 2 us per try: about 2 s
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-  unsigned done;
-  // the thread may sleep up to 2 us inside try_wait until the phase completes
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 2000;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-  return done != 0;
-}
-__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
-      ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
-        "r"(bar) : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];\n"
-      ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2),
-        "r"(bar) : "memory");
-}
 
 template <int BY, int BX>
 struct TmaLayout {
@@ -175,23 +65,6 @@ struct TmaLayout {
   template <typename S>
   __host__ __device__ static constexpr int slot_bytes() { return 7 * pop_bytes<S>(); }
 };
-
-__device__ __forceinline__ void mbar_init_count(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-// Named barrier that also returns the OR of v over the participating threads, so every
-// thread takes the same decision.
-__device__ __forceinline__ bool named_sync_or(int id, int threads, bool v) {
-  unsigned r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
-      " barrier.cta.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(r) : "r"((unsigned)v), "r"(id), "r"(threads) : "memory");
-  return r != 0;
-}
 
 // Fused step, TMA-staged.  CTA = BY + 2 consumer warps + 1 producer warp.  Consumer warp w
 // stands for lattice row q1 = y0 - 1 + w (warps 0 and BY + 1 are halo rows; they also compute
@@ -697,6 +570,9 @@ StepArgs<S> make_args(Grid* g, int src) {
   a.cap = g->cap;
   a.counters = g->counters;
   a.nblocks = g->grid_dim.x * g->grid_dim.y * g->grid_dim.z;
+  a.pitch = g->pitch ? g->pitch : g->d.n[1];
+  a.col0 = g->col0;
+  a.ps = pop_stride(g);
   return a;
 }
 
@@ -787,9 +663,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                   CUtensorMapFloatOOBfill);
 
-// Tensor maps of the two population buffers (4-D: q2, q1, q3, population) with the main
-// (bx x BY+2) and halo (V x BY+2) boxes, and of the coefficient table (3-D: slot, q1, q3).
-bool build_tmaps(Grid* g, int by, int bx) {
+EncodeTiledFn tiled_encoder() {
   static EncodeTiledFn encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -797,10 +671,18 @@ bool build_tmaps(Grid* g, int by, int bx) {
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
             cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
       cudaGetLastError();
-      return false;
+      return nullptr;
     }
     encode = reinterpret_cast<EncodeTiledFn>(fn);
   }
+  return encode;
+}
+
+// Tensor maps of the two population buffers (4-D: q2, q1, q3, population) with the main
+// (bx x BY+2) and halo (V x BY+2) boxes, and of the coefficient table (3-D: slot, q1, q3).
+bool build_tmaps(Grid* g, int by, int bx) {
+  const EncodeTiledFn encode = tiled_encoder();
+  if (!encode) return false;
   const int es = (int)g->elem, rs = g->d.prec == LBW_F64 ? 8 : 4;
   CUtensorMapDataType dt = g->d.prec == LBW_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                            : g->d.prec == LBW_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -914,11 +796,16 @@ __global__ void init_f_kernel(const StepArgs<S> a, const typename Store<S>::R* _
     const R e = R(0.5) * a.cs2 * rho;
     R o[7] = {R(0.5) * a.two_w0 * rho, e + R(0.5) * j1, e - R(0.5) * j1, e + R(0.5) * j2,
               e - R(0.5) * j2, e + R(0.5) * j3, e - R(0.5) * j3};
+    const long long px = ((long long)q3 * a.n1 + q1) * a.pitch + a.col0 + q2;
+    // ghost copy of a node near the periodic wrap (padded storage only)
+    int gq = -1;
+    if (a.col0 > 0 && p2) gq = q2 < a.col0 ? a.col0 + a.n2 + q2 : (q2 >= a.n2 - a.col0 ? q2 - a.n2 + a.col0 : -1);
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
       R v = o[i];
       if (Store<S>::kScaled) v *= a.inv_w[i];
-      Store<S>::st(a.fout + (long long)i * a.nn + x, v);
+      Store<S>::st(a.fout + (long long)i * a.ps + px, v);
+      if (gq >= 0) Store<S>::st(a.fout + (long long)i * a.ps + (px - a.col0 - q2) + gq, v);
     }
   }
 }
@@ -947,17 +834,26 @@ cudaError_t launch_init_t(Grid* g, const double* d_pulses, int npulse) {
 
 // ---------------------------------------------------------------- read-out ---------------
 
+// Storage address of dense node x (q2 fastest) in a possibly padded layout.
+struct Pad {
+  int n2, pitch, col0;
+  __device__ long long at(long long x) const {
+    return (x / n2) * pitch + col0 + (x % n2);
+  }
+};
+
 template <typename S>
-__global__ void field_kernel(const S* __restrict__ f, long long nn, int n1, int n2,
-                             const typename Store<S>::R* __restrict__ tab, double w0,
-                             double w1, double* __restrict__ P) {
+__global__ void field_kernel(const S* __restrict__ f, long long nn, long long ps, Pad pad, int n1,
+                             const typename Store<S>::R* __restrict__ tab, double w0, double w1,
+                             double* __restrict__ P) {
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < nn;
        x += (long long)gridDim.x * blockDim.x) {
-    const int q1 = (int)((x / n2) % n1);
-    const int q3 = (int)(x / ((long long)n1 * n2));
+    const int q1 = (int)((x / pad.n2) % n1);
+    const int q3 = (int)(x / ((long long)n1 * pad.n2));
+    const long long px = pad.at(x);
     double r = 0.0;
     for (int i = 0; i < 7; ++i) {
-      double v = (double)Store<S>::ld(f + (long long)i * nn + x);
+      double v = (double)Store<S>::ld(f + (long long)i * ps + px);
       if (Store<S>::kScaled) v *= (i == 0 ? w0 : w1);
       r += v;
     }
@@ -966,24 +862,35 @@ __global__ void field_kernel(const S* __restrict__ f, long long nn, int n1, int 
 }
 
 template <typename S>
-__global__ void to_double_kernel(const S* __restrict__ f, long long nn, double w0, double w1,
-                                 double* __restrict__ out) {
+__global__ void to_double_kernel(const S* __restrict__ f, long long nn, long long ps, Pad pad,
+                                 double w0, double w1, double* __restrict__ out) {
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < 7 * nn;
        x += (long long)gridDim.x * blockDim.x) {
-    double v = (double)Store<S>::ld(f + x);
-    if (Store<S>::kScaled) v *= (x < nn ? w0 : w1);
+    const long long i = x / nn, node = x - i * nn;
+    double v = (double)Store<S>::ld(f + i * ps + pad.at(node));
+    if (Store<S>::kScaled) v *= (i == 0 ? w0 : w1);
     out[x] = v;
   }
 }
 
+// Dense doubles into storage; padded storage also gets the ghost copies of a periodic q2.
 template <typename S>
-__global__ void from_double_kernel(const double* __restrict__ in, long long nn, double w0,
-                                   double w1, S* __restrict__ f) {
+__global__ void from_double_kernel(const double* __restrict__ in, long long nn, long long ps,
+                                   Pad pad, bool p2, double w0, double w1, S* __restrict__ f) {
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < 7 * nn;
        x += (long long)gridDim.x * blockDim.x) {
+    const long long i = x / nn, node = x - i * nn;
     double v = in[x];
-    if (Store<S>::kScaled) v /= (x < nn ? w0 : w1);
-    Store<S>::st(f + x, (typename Store<S>::R)v);
+    if (Store<S>::kScaled) v /= (i == 0 ? w0 : w1);
+    const long long px = pad.at(node);
+    const typename Store<S>::R r = (typename Store<S>::R)v;
+    Store<S>::st(f + i * ps + px, r);
+    if (pad.col0 > 0 && p2) {
+      const int q2 = (int)(node % pad.n2);
+      const long long row = px - pad.col0 - q2;
+      if (q2 < pad.col0) Store<S>::st(f + i * ps + row + pad.col0 + pad.n2 + q2, r);
+      if (q2 >= pad.n2 - pad.col0) Store<S>::st(f + i * ps + row + q2 - pad.n2 + pad.col0, r);
+    }
   }
 }
 
@@ -992,15 +899,18 @@ cudaError_t launch_readout_t(Grid* g, int what, double* d_out, const double* d_i
   const int threads = 256;
   const int blocks = 152 * 8;
   const S* f = reinterpret_cast<const S*>(g->f[g->cur]);
+  const Pad pad{g->d.n[1], g->pitch ? g->pitch : g->d.n[1], g->col0};
+  const long long ps = pop_stride(g);
   if (what == 0)
     field_kernel<S><<<blocks, threads, 0, g->stream>>>(
-        f, g->nn, g->d.n[0], g->d.n[1], reinterpret_cast<const typename Store<S>::R*>(g->table),
+        f, g->nn, ps, pad, g->d.n[0], reinterpret_cast<const typename Store<S>::R*>(g->table),
         g->w0, g->w1, d_out);
   else if (what == 1)
-    to_double_kernel<S><<<blocks, threads, 0, g->stream>>>(f, g->nn, g->w0, g->w1, d_out);
+    to_double_kernel<S><<<blocks, threads, 0, g->stream>>>(f, g->nn, ps, pad, g->w0, g->w1, d_out);
   else
     from_double_kernel<S><<<blocks, threads, 0, g->stream>>>(
-        d_in, g->nn, g->w0, g->w1, reinterpret_cast<S*>(g->f[g->cur]));
+        d_in, g->nn, ps, pad, g->d.bc[2] == LBW_BC_PERIODIC, g->w0, g->w1,
+        reinterpret_cast<S*>(g->f[g->cur]));
   return cudaGetLastError();
 }
 
@@ -1015,6 +925,27 @@ cudaError_t dispatch(int prec, F&& fn) {
 }
 
 }  // namespace
+
+bool encode_tiled_map(void* map, int prec, int rank, void* base, const uint64_t* dims,
+                      const uint64_t* strides, const uint32_t* box) {
+  const EncodeTiledFn encode = tiled_encoder();
+  if (!encode) return false;
+  const CUtensorMapDataType dt = prec == LBW_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : prec == LBW_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : prec == LBW_F16S ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  cuuint64_t d[5], st[4];
+  cuuint32_t bx[5], es[5];
+  for (int k = 0; k < rank; ++k) {
+    d[k] = dims[k];
+    bx[k] = box[k];
+    es[k] = 1;
+    if (k + 1 < rank) st[k] = strides[k];
+  }
+  return encode(reinterpret_cast<CUtensorMap*>(map), dt, (cuuint32_t)rank, base, d, st, bx, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 cudaError_t launch_step(Grid* g, int src) {
   return dispatch(g->d.prec, [&](auto tag) { return launch_step_t<decltype(tag)>(g, src); });
