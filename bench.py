@@ -222,6 +222,29 @@ def run_ensemble(args):
     h2d = sum(np.asarray(p).nbytes for p in pulses) + probes_q.astype(np.int32).nbytes
     d2h = series.nbytes + 2 * 8 * 8 * len(specs)
     b.close()
+    sequential = None
+    if args.vs_sequential > 0:
+        # the same members one after another, each its own lattice on the single-lattice path
+        sub = specs[: args.vs_sequential]
+        grids = [lbw.Grid(s_, stream=sh) for s_ in sub]
+        for g_, p_ in zip(grids, pulses):
+            g_.init(p_)
+            g_.step(8)
+        stream.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for g_ in grids:
+            g_.step(lbm_steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        seq_ms = ev0.elapsed_time(ev1)
+        sub_nodes = sum(s_.nodes for s_ in sub)
+        seq = sub_nodes * lbm_steps / (seq_ms / 1e3) / 1e6
+        sequential = {"members": len(sub), "mlups": seq,
+                      "batched_step_mlups": nodes * lbm_steps * args.steps / (sum(stp) / 1e3) / 1e6}
+        sequential["batched_over_sequential"] = sequential["batched_step_mlups"] / seq
+        for g_ in grids:
+            g_.close()
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -256,6 +279,8 @@ def run_ensemble(args):
         "clocks": clk.summary(),
         "gpu_launches": launches,
     }
+    if sequential is not None:
+        line["vs_sequential"] = sequential
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -324,6 +349,9 @@ def main():
                     choices=["cylinder", "disk", "trumpet", "torus", "ensemble"])
     ap.add_argument("--members", type=int, default=512,
                     help="ensemble members (--workload ensemble)")
+    ap.add_argument("--vs-sequential", type=int, default=0, metavar="M",
+                    help="ensemble: also time the first M members advanced one after another as "
+                         "single lattices (the plain path) and report both rates")
     ap.add_argument("--vs-f64", action="store_true",
                     help="after the timed region, rerun the workload with FP64 storage on the "
                          "GPU and report the field and mode-frequency deviations")

@@ -109,7 +109,9 @@ lbw_status lbw_init(lbw_grid* g, const lbw_pulse* host_pulses, int32_t n_pulses)
 
 /* Advance n_steps >= 0 time steps (one fused stream + collide launch per step, captured in
  * CUDA graphs).  Asynchronous on the grid's stream; registered probes record P after each
- * step's streaming. */
+ * step's streaming.  Every device wait inside a step is bounded: if one runs out, the kernel
+ * raises a flag instead of hanging, and the next call that synchronises (lbw_probe_read,
+ * lbw_spectrum, lbw_get_field, lbw_get_populations) returns LBW_ETIMEOUT until lbw_init. */
 lbw_status lbw_step(lbw_grid* g, int64_t n_steps);
 
 /* Register n (0 <= n <= 64) probe nodes, host_q = n x (q1, q2, q3), with room for

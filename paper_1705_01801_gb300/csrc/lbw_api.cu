@@ -246,6 +246,18 @@ lbw_status ensure_graph(Grid* g, int start, int len) {
   return LBW_OK;
 }
 
+// Samples recorded so far (counters[1]) and the wait flag (counters[3]): a step whose bounded
+// wait for staged data ran out raises the flag and leaves the state undefined.
+lbw_status read_counters(Grid* g, unsigned long long* recorded) {
+  unsigned long long c[3] = {0, 0, 0};
+  LBW_CUDA(cudaMemcpyAsync(c, g->counters + 1, sizeof(c), cudaMemcpyDeviceToHost, g->stream));
+  LBW_CUDA(cudaStreamSynchronize(g->stream));
+  if (recorded) *recorded = c[0];
+  if (c[2]) return fail(LBW_ETIMEOUT, "a time step's bounded wait for staged data ran out; the state is "
+                                      "undefined until lbw_init");
+  return LBW_OK;
+}
+
 }  // namespace
 }  // namespace lbw
 
@@ -427,8 +439,8 @@ lbw_status lbw_probe(lbw_grid* g, const int32_t* host_q, int32_t n, int64_t capa
 lbw_status lbw_probe_read(lbw_grid* g, double* host_out, int64_t cap_per_probe, int64_t* n_steps) {
   if (!g || !n_steps) return fail(LBW_EINVAL, "NULL argument");
   unsigned long long rec = 0;
-  LBW_CUDA(cudaMemcpyAsync(&rec, g->counters + 1, sizeof(rec), cudaMemcpyDeviceToHost, g->stream));
-  LBW_CUDA(cudaStreamSynchronize(g->stream));
+  lbw_status st = read_counters(g, &rec);
+  if (st != LBW_OK) return st;
   *n_steps = (int64_t)rec;
   if (g->nprobe == 0) return LBW_OK;
   if (!host_out || cap_per_probe < (int64_t)rec)
@@ -451,8 +463,8 @@ lbw_status lbw_spectrum(lbw_grid* g, int32_t probe, int32_t k, double* host_freq
   if (probe < -1 || probe >= g->nprobe) return fail(LBW_EINVAL, "probe index out of range");
   if (k < 1 || k > 64) return fail(LBW_EINVAL, "1 <= k <= 64");
   unsigned long long rec = 0;
-  LBW_CUDA(cudaMemcpyAsync(&rec, g->counters + 1, sizeof(rec), cudaMemcpyDeviceToHost, g->stream));
-  LBW_CUDA(cudaStreamSynchronize(g->stream));
+  lbw_status st = read_counters(g, &rec);
+  if (st != LBW_OK) return st;
   if (rec < 4) return fail(LBW_ESTATE, "fewer than 4 recorded samples");
   const double* base = g->series + (probe >= 0 ? (size_t)probe * g->cap : 0);
   return spectrum_device(base, (int64_t)rec, probe >= 0 ? 1 : g->nprobe, (int32_t)g->cap,
@@ -493,7 +505,7 @@ lbw_status lbw_get_field(lbw_grid* g, double* host_P) {
   cudaFreeAsync(d, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_fail(e, "get_field");
-  return LBW_OK;
+  return read_counters(g, nullptr);
 }
 
 lbw_status lbw_get_populations(lbw_grid* g, double* host_f) {
@@ -506,7 +518,7 @@ lbw_status lbw_get_populations(lbw_grid* g, double* host_f) {
   cudaFreeAsync(d, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_fail(e, "get_populations");
-  return LBW_OK;
+  return read_counters(g, nullptr);
 }
 
 lbw_status lbw_set_populations(lbw_grid* g, const double* host_f) {

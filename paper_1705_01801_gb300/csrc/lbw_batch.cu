@@ -779,6 +779,17 @@ lbw_status advance(lbw_batch* b, int64_t n_steps) {
   return LBW_OK;
 }
 
+// Samples recorded (counters[1]) and the wait flag (counters[3]) of the ensemble.
+lbw_status batch_counters(lbw_batch* b, unsigned long long* recorded) {
+  unsigned long long c[3] = {0, 0, 0};
+  LBW_CUDA(cudaMemcpyAsync(c, b->counters + 1, sizeof(c), cudaMemcpyDeviceToHost, b->stream));
+  LBW_CUDA(cudaStreamSynchronize(b->stream));
+  if (recorded) *recorded = c[0];
+  if (c[2]) return fail(LBW_ETIMEOUT, "a time step's bounded wait for staged data ran out; the state is "
+                                      "undefined until lbw_batch_init");
+  return LBW_OK;
+}
+
 std::string signature(const lbw_batch* b) {
   unsigned long long h = 1469598103934665603ULL;  // FNV-1a over the members' sizes
   for (const Grid& g : b->views)
@@ -1002,8 +1013,8 @@ lbw_status lbw_batch_step(lbw_batch* b, int64_t n_steps) {
 lbw_status lbw_batch_probe_read(lbw_batch* b, double* host_out, int64_t* n_steps) {
   if (!b || !n_steps) return fail(LBW_EINVAL, "NULL argument");
   unsigned long long rec = 0;
-  LBW_CUDA(cudaMemcpyAsync(&rec, b->counters + 1, sizeof(rec), cudaMemcpyDeviceToHost, b->stream));
-  LBW_CUDA(cudaStreamSynchronize(b->stream));
+  lbw_status st = batch_counters(b, &rec);
+  if (st != LBW_OK) return st;
   *n_steps = (int64_t)rec;
   if (b->nprobe == 0 || rec == 0) return LBW_OK;
   if (!host_out) return fail(LBW_EINVAL, "host_out is NULL");
@@ -1019,8 +1030,8 @@ lbw_status lbw_batch_spectrum(lbw_batch* b, int32_t k, double* host_freq, double
   if (k < 1 || k > 64) return fail(LBW_EINVAL, "1 <= k <= 64");
   if (b->nprobe == 0) return fail(LBW_ESTATE, "no probes registered");
   unsigned long long rec = 0;
-  LBW_CUDA(cudaMemcpyAsync(&rec, b->counters + 1, sizeof(rec), cudaMemcpyDeviceToHost, b->stream));
-  LBW_CUDA(cudaStreamSynchronize(b->stream));
+  lbw_status st0 = batch_counters(b, &rec);
+  if (st0 != LBW_OK) return st0;
   if (rec < 4) return fail(LBW_ESTATE, "fewer than 4 recorded samples");
   for (int m = 0; m < b->n; ++m) {
     lbw_status st = spectrum_device(b->series + (size_t)m * b->nprobe * b->cap, (int64_t)rec, b->nprobe,
@@ -1044,7 +1055,7 @@ lbw_status lbw_batch_get_populations(lbw_batch* b, int32_t member, double* host_
   cudaFreeAsync(d, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "batch populations");
-  return LBW_OK;
+  return batch_counters(b, nullptr);
 }
 
 lbw_status lbw_batch_tune(lbw_batch* b, int32_t trial_steps, const char* cache_path, char* report,
