@@ -153,6 +153,46 @@ def test_cs2_is_a_free_parameter():
         assert abs(om / ck - 1) < 3e-3
 
 
+def _textbook_wave_lbm_step(f, cs2):
+    """One step of the plain Cartesian D3Q7 wave LBM at tau = 1/2, written out here: periodic
+    pull streaming, rho = sum f, j = sum f xi, f^eq = w (rho + xi . j / cs^2), f* = 2 f^eq - f.
+    State (7, N3, N1, N2); populations 1/2 = +-e1 (axis 1), 3/4 = +-e2 (axis 2), 5/6 = +-e3
+    (axis 0)."""
+    xi = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    axis_of = {0: 1, 1: 2, 2: 0}
+    g = np.empty_like(f)
+    for i, e in enumerate(xi):
+        v = f[i]
+        for a in range(3):
+            if e[a]:
+                v = np.roll(v, e[a], axis=axis_of[a])
+        g[i] = v
+    rho = g.sum(0)
+    j = [sum(e[a] * g[i] for i, e in enumerate(xi)) for a in range(3)]
+    w = W(cs2)
+    out = np.empty_like(f)
+    for i, e in enumerate(xi):
+        feq = w[i] * (rho + (e[0] * j[0] + e[1] * j[1] + e[2] * j[2]) / cs2)
+        out[i] = 2 * feq - g[i]
+    return out
+
+
+def test_identity_metric_reduces_to_cartesian_wave_lbm():
+    """With g = delta (G = 0, sqrt g = 1) and c = cs the geometric force vanishes identically
+    (c^2 g^{ab} - cs^2 delta^{ab} = 0), so the scheme must be the plain Cartesian wave LBM:
+    same populations after 12 steps from a random state, to rounding."""
+    cs2 = 0.25
+    spec = GridSpec(kind=KIND_CARTESIAN, n=(5, 6, 7), h=(1, 1, 1), x0=(0, 0, 0), c=0.5, cs2=cs2)
+    g = oracle.OracleGrid(spec)
+    f = np.random.default_rng(8).normal(size=(7, 7, 5, 6))
+    g.set_f(f)
+    g.step(12)
+    ref = f
+    for _ in range(12):
+        ref = _textbook_wave_lbm_step(ref, cs2)
+    np.testing.assert_allclose(g.get_f(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
 # ---------------------------------------------------------------- conservation ------------
 
 def test_mass_conservation_torus():
