@@ -72,6 +72,8 @@ def lib():
         L.lbwo_get_f.argtypes = [vp, dp]
         L.lbwo_set_f.argtypes = [vp, dp]
         L.lbwo_get_P.argtypes = [vp, dp]
+        L.lbwo_set_sources.argtypes = [vp, ip, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double]
         _lib = L
     return _lib
 
@@ -137,6 +139,13 @@ class OracleGrid:
         out = np.zeros((max(self._probes, 1), max(self._cap, 1)))
         n = self._L.lbwo_read_probes(self._h, _dp(out))
         return out[: self._probes, :n]
+
+    def set_sources(self, q, kind=0, amp=1.0, omega=0.0):
+        """Harmonic sources at lattice nodes q (n x 3): kind 0 imposes P = amp sin(omega t),
+        kind 1 imposes J'_z = amp sin(omega t), at the end of every time step t (reading R8 of
+        lbw_oracle.c)."""
+        q = np.ascontiguousarray(np.asarray(q, dtype=np.int32).reshape(-1, 3))
+        self._L.lbwo_set_sources(self._h, _ip(q), q.shape[0], int(kind), float(amp), float(omega))
 
     def get_f(self):
         """Post-collision populations, shape (7, N3, N1, N2)."""

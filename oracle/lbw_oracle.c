@@ -40,6 +40,10 @@
  *   R7 initial state at rest: J'(0) = 0 (Eq. JShifted), so the stored post-collision
  *      populations are f^eq(rho0, +F(rho0)/2).  Pinned by the finite-difference test (the
  *      naive f^eq(rho0, 0) start leaves an O(dt) velocity error: first-order convergence).
+ *   R8 harmonic sources (the paper imposes P, or J'_z for the plate, at source nodes): after
+ *      each step the source nodes' populations become the equilibrium carrying the imposed
+ *      value (apply_sources).  Pinned by the radiated cylindrical wave of a ring source
+ *      matching the radial Bessel equation's solutions.
  *   Also corrected from the printed formulas (verified symbolically): trumpet
  *   Gamma^theta_{z theta} = lambda / Zc (printed lambda / Zc^2) and torus
  *   Gamma^r_{theta theta} = -(R + r cos phi) cos phi (printed with +); the contracted
@@ -78,6 +82,11 @@ typedef struct {
   long long *probe_node;
   long long cap, nrec;
   double *series; /* [nprobe][cap] */
+  /* harmonic sources (reading R8 below) */
+  int nsrc, src_kind;
+  long long *src_node;
+  double src_amp, src_omega;
+  long long t; /* time steps since lbwo_init */
 } OGrid;
 
 static const int XI[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0},
@@ -214,7 +223,7 @@ void lbwo_destroy(void *p) {
   OGrid *g = (OGrid *)p;
   if (!g) return;
   free(g->f); free(g->fnew); free(g->fpull); free(g->rho);
-  free(g->probe_node); free(g->series);
+  free(g->probe_node); free(g->series); free(g->src_node);
   free(g);
 }
 
@@ -311,6 +320,37 @@ static void record_probes(OGrid *g) {
   g->nrec++;
 }
 
+/* Reading R8 (harmonic sources, Sec. IV: the ring, plate and point sources that impose
+ * P = C sin(omega t), or J'_z = C sin(omega t) for the plate, at their nodes): at the end of
+ * time step t (t = 1, 2, ... since lbwo_init) the post-collision populations of every source
+ * node are replaced by an equilibrium carrying the imposed value.
+ *   kind 0 (P source):   f*_i = f_i^eq(rho_s, j' = 0),  rho_s = sqrt(g) C sin(omega t);
+ *   kind 1 (J'_z source): f*_i = f_i^eq(rho, j' = (0, 0, sqrt(g) C sin(omega t))), rho = sum f*_i
+ *                         of the node (kept); the component is along q3. */
+static void apply_sources(OGrid *g, double *f) {
+  const double cs2 = g->cs2, w0 = 1.0 - 3.0 * cs2, w1 = 0.5 * cs2;
+  const double v = g->src_amp * sin(g->src_omega * (double)g->t);
+  for (int k = 0; k < g->nsrc; k++) {
+    long long x = g->src_node[k];
+    int q2 = (int)(x % g->n[1]);
+    int q1 = (int)((x / g->n[1]) % g->n[0]);
+    int q3 = (int)(x / ((long long)g->n[1] * g->n[0]));
+    double sg, gi[3][3], G[3];
+    geom_q(g, q1, q2, q3, &sg, gi, G);
+    double rho, j3;
+    if (g->src_kind == 0) {
+      rho = sg * v;
+      j3 = 0.0;
+    } else {
+      rho = 0.0;
+      for (int i = 0; i < 7; i++) rho += f[i * g->nn + x];
+      j3 = sg * v;
+    }
+    for (int i = 0; i < 7; i++)
+      f[i * g->nn + x] = (i == 0) ? w0 * rho : w1 * (rho + XI[i][2] * j3 / cs2);
+  }
+}
+
 static void one_step(OGrid *g) {
   const double c2 = g->c * g->c, cs2 = g->cs2;
   const double w0 = 1.0 - 3.0 * cs2, w1 = 0.5 * cs2;
@@ -353,6 +393,8 @@ static void one_step(OGrid *g) {
           g->fnew[i * g->nn + x] = 2.0 * feq - f[i];
         }
       }
+  g->t++;
+  apply_sources(g, g->fnew);
   double *t = g->f;
   g->f = g->fnew;
   g->fnew = t;
@@ -401,6 +443,20 @@ void lbwo_init(void *p, const double *pulses, int npulse) {
         }
       }
   g->nrec = 0;
+  g->t = 0;
+}
+
+/* Harmonic sources at n lattice nodes (q1, q2, q3); kind 0 = P source, 1 = J'_z source
+ * (reading R8).  n = 0 removes them. */
+void lbwo_set_sources(void *p, const int32_t *q, int n, int kind, double amp, double omega) {
+  OGrid *g = (OGrid *)p;
+  free(g->src_node);
+  g->nsrc = n;
+  g->src_kind = kind;
+  g->src_amp = amp;
+  g->src_omega = omega;
+  g->src_node = (long long *)malloc((n > 0 ? n : 1) * sizeof(long long));
+  for (int k = 0; k < n; k++) g->src_node[k] = nid(g, q[3 * k], q[3 * k + 1], q[3 * k + 2]);
 }
 
 void lbwo_step(void *p, long long nsteps) {

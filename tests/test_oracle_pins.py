@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from lbw_workloads import (BC_ANTIBOUNCE, BC_BOUNCE, BC_PERIODIC, KIND_CARTESIAN,
+from lbw_workloads import (BC_ANTIBOUNCE, BC_BOUNCE, BC_FREE, BC_PERIODIC, KIND_CARTESIAN,
                            KIND_CYLINDRICAL, KIND_POLAR, KIND_TOROIDAL, KIND_TRUMPET,
                            PROFILE_BESSEL, PROFILE_EXP, GridSpec, embedding)
 from modes import annulus_radial, annulus_wavenumbers, pipe_zeros
@@ -191,6 +191,61 @@ def test_identity_metric_reduces_to_cartesian_wave_lbm():
     for _ in range(12):
         ref = _textbook_wave_lbm_step(ref, cs2)
     np.testing.assert_allclose(g.get_f(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_ring_source_radiates_cylindrical_wave():
+    """Sec. IV.A, the cylindrical-wave benchmark: a ring source P = C sin(omega t) at r_min
+    radiates a wave whose profile, at a fixed time behind the front, solves the radial Bessel
+    equation of order 0 with k = omega / c (Eq. TheoreticalExpresion gives its J_0 form; the
+    outgoing wave is a J_0 + b Y_0 at any instant).  The least-squares fit must leave < 1.5%
+    residual, and the order-1 and plane-wave forms (a dropped 1/r term, a lost metric) must
+    fit several times worse."""
+    from scipy.special import j0, j1, y0, y1
+    n1, T, om, c = 400, 600, 0.05, 0.4
+    spec = GridSpec(kind=KIND_POLAR, n=(n1, 3, 1), h=(1, 2 * math.pi / 3, 1), x0=(1, 0, 0), c=c,
+                    bc=(BC_FREE, BC_FREE, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC))
+    g = oracle.OracleGrid(spec)
+    g.init(np.zeros((0, 5)))
+    g.set_sources([[0, j, 0] for j in range(3)], kind=0, amp=1.0, omega=om)
+    g.step(T)
+    P = g.get_P()[0, :, 0]
+    r = 1.5 + np.arange(n1)
+    k = om / c
+    sel = (r >= 10) & (r <= 0.5 * c * T)
+
+    def resid(cols):
+        A = np.stack([f(k * r[sel]) for f in cols], 1)
+        coef, *_ = np.linalg.lstsq(A, P[sel], rcond=None)
+        return np.sqrt(((P[sel] - A @ coef) ** 2).mean() / (P[sel] ** 2).mean())
+
+    e0 = resid([j0, y0])
+    assert e0 < 0.015
+    assert resid([j1, y1]) > 3 * e0
+    assert resid([np.cos, np.sin]) > 10 * e0
+
+
+def test_source_kinds_impose_their_values():
+    """Reading R8: after step t a P source node holds f^eq(sqrt(g) C sin(omega t), 0), a J'_z
+    source node keeps its rho and carries j'_3 = sqrt(g) C sin(omega t)."""
+    spec = GridSpec(kind=KIND_CYLINDRICAL, n=(6, 8, 5), h=(1, 2 * math.pi / 8, 1), x0=(3, 0, 0),
+                    c=0.4, bc=(BC_BOUNCE, BC_BOUNCE, BC_PERIODIC, BC_PERIODIC, BC_BOUNCE, BC_BOUNCE))
+    cs2 = 0.25
+    w = W(cs2)
+    for kind in (0, 1):
+        g = oracle.OracleGrid(spec)
+        g.init([[4.0, 0.5, 2.0, 1.5, 1.0]])
+        g.set_sources([[2, 3, 1]], kind=kind, amp=0.7, omega=0.3)
+        g.step(9)
+        f = g.get_f()[:, 1, 2, 3]
+        sg = g.geometry(3 + 2.5, 3.5 * 2 * math.pi / 8, 1.5)[0]  # sqrt(g) (h = 1 except theta)
+        sg *= 2 * math.pi / 8
+        v = 0.7 * math.sin(0.3 * 9)
+        if kind == 0:
+            np.testing.assert_allclose(f, w * sg * v, rtol=1e-12)
+        else:
+            rho = f.sum()
+            assert (f[5] - f[6]) == pytest.approx(2 * w[5] * sg * v / cs2, rel=1e-12)
+            np.testing.assert_allclose(f[:5], w[:5] * rho, rtol=1e-12)
 
 
 # ---------------------------------------------------------------- conservation ------------
