@@ -114,6 +114,17 @@ lbw_status lbw_init(lbw_grid* g, const lbw_pulse* host_pulses, int32_t n_pulses)
  * lbw_spectrum, lbw_get_field, lbw_get_populations) returns LBW_ETIMEOUT until lbw_init. */
 lbw_status lbw_step(lbw_grid* g, int64_t n_steps);
 
+/* Harmonic sources (Sec. IV: the ring, plate and point sources that drive the pipe, horn
+ * and torus): after every subsequent time step t (counted from lbw_init), each of the n
+ * source nodes host_q = n x (q1, q2, q3) takes the equilibrium populations that carry
+ * amp sin(omega t): kind 0 imposes P = amp sin(omega t) (f = f^eq(sqrt(g) P, 0)), kind 1
+ * imposes J'_z (the q3 component of J') = amp sin(omega t) and keeps the node's rho.
+ * omega in rad / step.  n = 0 removes the sources.  LBW_EINVAL for nodes outside the lattice
+ * or kind not 0 / 1.  Without sources a step is a single kernel launch; with sources a small
+ * second launch per step applies them. */
+lbw_status lbw_source(lbw_grid* g, const int32_t* host_q, int32_t n, int32_t kind, double amp,
+                      double omega);
+
 /* Register n (0 <= n <= 64) probe nodes, host_q = n x (q1, q2, q3), with room for
  * `capacity` samples each (further samples are dropped).  Resets the series. */
 lbw_status lbw_probe(lbw_grid* g, const int32_t* host_q, int32_t n, int64_t capacity);
@@ -192,6 +203,13 @@ lbw_status lbw_batch_probe(lbw_batch* b, const int32_t* host_q, int32_t per_memb
 
 /* Advance every member by n_steps (asynchronous on the ensemble's stream). */
 lbw_status lbw_batch_step(lbw_batch* b, int64_t n_steps);
+
+/* Harmonic sources for every member (see lbw_source): per_member nodes each, host_q =
+ * n x per_member x (q1, q2, q3) in the members' own lattices, one angular frequency per member
+ * (host_omega[n], rad / step), a common kind and amplitude.  A frequency sweep is one ensemble
+ * of identical geometries with different omegas.  per_member = 0 removes the sources. */
+lbw_status lbw_batch_source(lbw_batch* b, const int32_t* host_q, int32_t per_member, int32_t kind,
+                            double amp, const double* host_omega);
 
 /* All series: host_out = n x per_member x capacity doubles; *n_steps = samples recorded. */
 lbw_status lbw_batch_probe_read(lbw_batch* b, double* host_out, int64_t* n_steps);

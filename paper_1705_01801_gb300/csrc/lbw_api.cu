@@ -210,6 +210,8 @@ lbw_status build_table(const lbw_grid_desc& d, std::vector<double>& tab) {
 lbw_status validate_desc(lbw_grid_desc& d) { return validate(d); }
 lbw_status build_force_table(const lbw_grid_desc& d, std::vector<double>& tab) { return build_table(d, tab); }
 
+double lattice_sqrtg(const lbw_grid_desc& d, int q1, int q3) { return metric_at(d, q1, 0, q3).sg; }
+
 namespace {
 
 size_t elem_size(int prec) { return prec == LBW_F64 ? 8 : prec == LBW_F32 ? 4 : 2; }
@@ -224,6 +226,13 @@ void drop_graphs(Grid* g) {
   g->graph_len = 0;
 }
 
+// Harmonic sources on the state just written to buffer `buf` (no-op without sources).
+cudaError_t apply_sources(Grid* g, int buf) {
+  if (g->nsrc == 0) return cudaSuccess;
+  return launch_sources(g->d.prec, g->f[buf], static_cast<const SourceEntry*>(g->src), g->nsrc,
+                        g->src_kind, g->src_amp, g->counters, g->stream);
+}
+
 // A chain of `len` steps starting from buffer `start`, captured once and replayed.
 lbw_status ensure_graph(Grid* g, int start, int len) {
   if (g->graph[start] && g->graph_len == len) return LBW_OK;
@@ -234,6 +243,7 @@ lbw_status ensure_graph(Grid* g, int start, int len) {
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < len && e == cudaSuccess; ++s) {
     e = launch_step(g, src);
+    if (e == cudaSuccess) e = apply_sources(g, 1 - src);
     src = 1 - src;
   }
   cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
@@ -342,6 +352,7 @@ void lbw_destroy(lbw_grid* g) {
   if (g->counters) cudaFreeAsync(g->counters, g->stream);
   if (g->probe_q) cudaFreeAsync(g->probe_q, g->stream);
   if (g->series) cudaFreeAsync(g->series, g->stream);
+  if (g->src) cudaFreeAsync(g->src, g->stream);
   cudaStreamSynchronize(g->stream);
   if (g->own_stream) cudaStreamDestroy(g->stream);
   delete g;
@@ -394,6 +405,7 @@ lbw_status lbw_step(lbw_grid* g, int64_t n_steps) {
   }
   while (left > 0) {
     LBW_CUDA(launch_step(g, g->cur));
+    LBW_CUDA(apply_sources(g, 1 - g->cur));
     g->cur = 1 - g->cur;
     --left;
   }
@@ -404,6 +416,40 @@ lbw_status lbw_step(lbw_grid* g, int64_t n_steps) {
 lbw_status lbw_step_count(lbw_grid* g, int64_t* out) {
   if (!g || !out) return fail(LBW_EINVAL, "NULL argument");
   *out = g->steps;
+  return LBW_OK;
+}
+
+lbw_status lbw_source(lbw_grid* g, const int32_t* host_q, int32_t n, int32_t kind, double amp,
+                      double omega) {
+  if (!g) return fail(LBW_EINVAL, "grid is NULL");
+  if (n < 0 || n > (1 << 24)) return fail(LBW_EINVAL, "0 <= n <= 2^24 source nodes");
+  if (n > 0 && !host_q) return fail(LBW_EINVAL, "host_q is NULL");
+  if (kind != 0 && kind != 1) return fail(LBW_EINVAL, "kind must be 0 (P) or 1 (J'_z)");
+  if (!std::isfinite(amp) || !std::isfinite(omega)) return fail(LBW_EINVAL, "amp and omega must be finite");
+  std::vector<SourceEntry> h((size_t)std::max(n, 0));
+  for (int k = 0; k < n; ++k) {
+    const int q1 = host_q[3 * k], q2 = host_q[3 * k + 1], q3 = host_q[3 * k + 2];
+    if (q1 < 0 || q1 >= g->d.n[0] || q2 < 0 || q2 >= g->d.n[1] || q3 < 0 || q3 >= g->d.n[2])
+      return fail(LBW_EINVAL, "source node outside the lattice");
+    h[k].off = ((long long)q3 * g->d.n[0] + q1) * g->d.n[1] + q2;
+    h[k].ps = g->nn;
+    h[k].ghost = 0;
+    h[k].pad = 0;
+    h[k].sg = lattice_sqrtg(g->d, q1, q3);
+    h[k].omega = omega;
+    h[k].cs2 = g->d.cs2;
+  }
+  drop_graphs(g);  // captured chains carry the source list
+  if (g->src) { cudaFreeAsync(g->src, g->stream); g->src = nullptr; }
+  g->nsrc = 0;
+  if (n > 0) {
+    LBW_CUDA(cudaMallocAsync(&g->src, sizeof(SourceEntry) * n, g->stream));
+    LBW_CUDA(cudaMemcpyAsync(g->src, h.data(), sizeof(SourceEntry) * n, cudaMemcpyHostToDevice, g->stream));
+    LBW_CUDA(cudaStreamSynchronize(g->stream));
+    g->nsrc = n;
+    g->src_kind = kind;
+    g->src_amp = amp;
+  }
   return LBW_OK;
 }
 

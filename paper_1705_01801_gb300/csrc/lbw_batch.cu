@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -525,6 +526,10 @@ struct lbw_batch {
   long long total_nodes = 0;
   bool tma = false;              // padded members on the TMA-staged kernel
   void* maps = nullptr;          // device: per member tensor maps (buffer 0, buffer 1, table)
+  // harmonic sources of all members (offsets from the buffer base), applied after each step
+  int nsrc = 0, src_kind = 0;
+  double src_amp = 0.0;
+  void* src = nullptr;
 };
 
 namespace {
@@ -736,6 +741,12 @@ cudaError_t launch_batch(lbw_batch* b, int src) {
   }
 }
 
+cudaError_t batch_sources(lbw_batch* b, int buf) {
+  if (b->nsrc == 0) return cudaSuccess;
+  return launch_sources(b->prec, b->f[buf], static_cast<const SourceEntry*>(b->src), b->nsrc, b->src_kind,
+                        b->src_amp, b->counters, b->stream);
+}
+
 lbw_status ensure_graph(lbw_batch* b, int start, int len) {
   if (b->graph[start] && b->graph_len == len) return LBW_OK;
   if (b->graph_len != len) drop_graphs(b);
@@ -745,6 +756,7 @@ lbw_status ensure_graph(lbw_batch* b, int start, int len) {
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < len && e == cudaSuccess; ++s) {
     e = launch_batch(b, src);
+    if (e == cudaSuccess) e = batch_sources(b, 1 - src);
     src = 1 - src;
   }
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
@@ -772,6 +784,7 @@ lbw_status advance(lbw_batch* b, int64_t n_steps) {
   }
   while (left > 0) {
     LBW_CUDA(launch_batch(b, b->cur));
+    LBW_CUDA(batch_sources(b, 1 - b->cur));
     b->cur = 1 - b->cur;
     --left;
   }
@@ -930,6 +943,7 @@ void lbw_batch_destroy(lbw_batch* b) {
   if (b->counters) cudaFreeAsync(b->counters, b->stream);
   if (b->items) cudaFreeAsync(b->items, b->stream);
   if (b->maps) cudaFreeAsync(b->maps, b->stream);
+  if (b->src) cudaFreeAsync(b->src, b->stream);
   if (b->probe_q) cudaFreeAsync(b->probe_q, b->stream);
   if (b->series) cudaFreeAsync(b->series, b->stream);
   cudaStreamSynchronize(b->stream);
@@ -1000,6 +1014,52 @@ lbw_status lbw_batch_probe(lbw_batch* b, const int32_t* host_q, int32_t per_memb
   lbw_status st = refresh(b);
   if (st != LBW_OK) return st;
   LBW_CUDA(cudaStreamSynchronize(b->stream));
+  return LBW_OK;
+}
+
+lbw_status lbw_batch_source(lbw_batch* b, const int32_t* host_q, int32_t per_member, int32_t kind,
+                            double amp, const double* host_omega) {
+  if (!b) return fail(LBW_EINVAL, "batch is NULL");
+  if (per_member < 0 || (long long)per_member * b->n > (1 << 24)) return fail(LBW_EINVAL, "too many source nodes");
+  if (per_member > 0 && (!host_q || !host_omega)) return fail(LBW_EINVAL, "sources need nodes and frequencies");
+  if (kind != 0 && kind != 1) return fail(LBW_EINVAL, "kind must be 0 (P) or 1 (J'_z)");
+  if (!std::isfinite(amp)) return fail(LBW_EINVAL, "amp must be finite");
+  const bool p_all = b->tma;  // padded members carry ghost copies of nodes near the wrap
+  std::vector<SourceEntry> h;
+  h.reserve((size_t)b->n * per_member);
+  for (int m = 0; m < b->n && per_member > 0; ++m) {
+    const Grid& g = b->views[m];
+    if (!std::isfinite(host_omega[m])) return fail(LBW_EINVAL, "omega must be finite");
+    const int pitch = g.pitch ? g.pitch : g.d.n[1], col0 = g.col0, n2 = g.d.n[1];
+    for (int k = 0; k < per_member; ++k) {
+      const int32_t* q = host_q + ((size_t)m * per_member + k) * 3;
+      if (q[0] < 0 || q[0] >= g.d.n[0] || q[1] < 0 || q[1] >= n2 || q[2] < 0 || q[2] >= g.d.n[2])
+        return fail(LBW_EINVAL, "source node outside its member's lattice");
+      SourceEntry e{};
+      e.off = (long long)b->foff[m] + ((long long)q[2] * g.d.n[0] + q[0]) * pitch + col0 + q[1];
+      e.ps = pop_stride(&g);
+      e.ghost = 0;
+      if (p_all && col0 > 0 && g.d.bc[2] == LBW_BC_PERIODIC) {
+        if (q[1] < col0) e.ghost = n2;
+        else if (q[1] >= n2 - col0) e.ghost = -n2;
+      }
+      e.sg = lattice_sqrtg(g.d, q[0], q[2]);
+      e.omega = host_omega[m];
+      e.cs2 = g.d.cs2;
+      h.push_back(e);
+    }
+  }
+  drop_graphs(b);  // captured chains carry the source list
+  if (b->src) { cudaFreeAsync(b->src, b->stream); b->src = nullptr; }
+  b->nsrc = 0;
+  if (!h.empty()) {
+    LBW_CUDA(cudaMallocAsync(&b->src, sizeof(SourceEntry) * h.size(), b->stream));
+    LBW_CUDA(cudaMemcpyAsync(b->src, h.data(), sizeof(SourceEntry) * h.size(), cudaMemcpyHostToDevice, b->stream));
+    LBW_CUDA(cudaStreamSynchronize(b->stream));
+    b->nsrc = (int)h.size();
+    b->src_kind = kind;
+    b->src_amp = amp;
+  }
   return LBW_OK;
 }
 

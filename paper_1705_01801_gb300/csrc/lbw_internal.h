@@ -53,6 +53,11 @@ struct Grid {
   // padded storage (ensembles on the tile kernel): row length and first data column in
   // elements; pitch 0 means dense rows of n2 values
   int pitch = 0, col0 = 0;
+  // harmonic sources: device SourceEntry array, applied after every step
+  int32_t nsrc = 0;
+  void* src = nullptr;
+  int32_t src_kind = 0;
+  double src_amp = 0.0;
   alignas(64) unsigned char tmaps[5 * 128];  // tensor maps: f[0] main/halo, f[1] main/halo, table
   dim3 grid_dim;
   // captured step chains, one per parity of the starting buffer
@@ -77,6 +82,18 @@ lbw_status cuda_fail(cudaError_t e, const char* what);
 lbw_status validate_desc(lbw_grid_desc& d);
 lbw_status build_force_table(const lbw_grid_desc& d, std::vector<double>& tab);
 
+// One harmonic source node: element offset of its population 0 from the buffer base, the
+// population stride, the column shift of its ghost copy (0: none), sqrt(g) in lattice
+// coordinates, the angular frequency (rad / step) and the lattice's cs^2.
+struct SourceEntry {
+  long long off, ps;
+  int ghost, pad;
+  double sg, omega, cs2;
+};
+
+// sqrt(g) of lattice node (q1, q3) of desc in lattice coordinates (FP64, as in the table)
+double lattice_sqrtg(const lbw_grid_desc& d, int q1, int q3);
+
 // population stride of a lattice's storage in elements
 inline long long pop_stride(const Grid* g) {
   return g->pitch ? (long long)g->d.n[0] * g->d.n[2] * g->pitch : g->nn;
@@ -89,6 +106,10 @@ cudaError_t launch_field(Grid* g, double* d_P);        // P of the current state
 cudaError_t launch_to_double(Grid* g, double* d_f);    // current populations -> doubles
 cudaError_t launch_from_double(Grid* g, const double* d_f);
 void step_launch_shape(Grid* g);                       // choose bx, by, lz, grid_dim
+// After step t (counters[0] = t): every source node's populations become the equilibrium that
+// carries amp sin(omega t) as P (kind 0) or as J'_z (kind 1).
+cudaError_t launch_sources(int prec, void* base, const SourceEntry* d_entries, int n, int kind,
+                           double amp, const unsigned long long* d_counters, cudaStream_t stream);
 // 128-byte CUtensorMap for a tiled TMA view: element type from lbw_prec, dims / box innermost
 // first, strides in bytes of dimensions 1 .. rank - 1; false when the driver refuses it
 bool encode_tiled_map(void* map, int prec, int rank, void* base, const uint64_t* dims,

@@ -832,6 +832,44 @@ cudaError_t launch_init_t(Grid* g, const double* d_pulses, int npulse) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- harmonic sources -------
+
+// Reading of the paper's sources (ring, plate and point sources of Sec. IV impose P, or J'_z
+// for the plate, as C sin(omega t)): after step t the source node's post-collision
+// populations are replaced by the equilibrium carrying the imposed value; kind 0:
+// f_i = f_i^eq(sqrt(g) C sin(omega t), 0); kind 1: f_i = f_i^eq(rho, (0, 0, sqrt(g) C sin(omega t)))
+// with the node's own rho.  16-bit formats store f_i / w_i.
+template <typename S>
+__global__ void source_kernel(S* __restrict__ base, const SourceEntry* __restrict__ e, int n, int kind,
+                              double amp, const unsigned long long* __restrict__ counters) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const SourceEntry s = e[k];
+  const double cs2 = s.cs2;
+  const double w0 = 1.0 - 3.0 * cs2, w1 = 0.5 * cs2;
+  const double v = amp * sin(s.omega * (double)counters[0]);
+  S* f = base + s.off;
+  double rho = 0.0, j3 = 0.0;
+  if (kind == 0) {
+    rho = s.sg * v;
+  } else {
+    for (int i = 0; i < 7; ++i) {
+      double x = (double)Store<S>::ld(f + (long long)i * s.ps);
+      if (Store<S>::kScaled) x *= (i == 0 ? w0 : w1);
+      rho += x;
+    }
+    j3 = s.sg * v;
+  }
+  for (int i = 0; i < 7; ++i) {
+    const double xi3 = i == 5 ? 1.0 : (i == 6 ? -1.0 : 0.0);
+    double val = i == 0 ? w0 * rho : w1 * (rho + xi3 * j3 / cs2);
+    if (Store<S>::kScaled) val /= (i == 0 ? w0 : w1);
+    const typename Store<S>::R r = (typename Store<S>::R)val;
+    Store<S>::st(f + (long long)i * s.ps, r);
+    if (s.ghost != 0) Store<S>::st(f + (long long)i * s.ps + s.ghost, r);
+  }
+}
+
 // ---------------------------------------------------------------- read-out ---------------
 
 // Storage address of dense node x (q2 fastest) in a possibly padded layout.
@@ -925,6 +963,18 @@ cudaError_t dispatch(int prec, F&& fn) {
 }
 
 }  // namespace
+
+cudaError_t launch_sources(int prec, void* base, const SourceEntry* d_entries, int n, int kind,
+                           double amp, const unsigned long long* d_counters, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int threads = 128, blocks = (n + threads - 1) / threads;
+  return dispatch(prec, [&](auto tag) {
+    using S = decltype(tag);
+    source_kernel<S><<<blocks, threads, 0, stream>>>(reinterpret_cast<S*>(base), d_entries, n, kind, amp,
+                                                     d_counters);
+    return cudaGetLastError();
+  });
+}
 
 bool encode_tiled_map(void* map, int prec, int rank, void* base, const uint64_t* dims,
                       const uint64_t* strides, const uint32_t* box) {

@@ -21,8 +21,8 @@ STATUS_NAMES = ["LBW_OK", "LBW_EINVAL", "LBW_ENOMEM", "LBW_ECUDA", "LBW_EUNSTABL
 # every symbol the header declares (checked by tests/test_abi.py)
 EXPORTS = ["lbw_create_grid", "lbw_init", "lbw_step", "lbw_probe", "lbw_probe_read",
            "lbw_spectrum", "lbw_spectrum_series", "lbw_spectrum_series_static", "lbw_get_field", "lbw_get_populations",
-           "lbw_set_populations", "lbw_step_count", "lbw_destroy", "lbw_last_error",
-           "lbw_batch_create", "lbw_batch_init", "lbw_batch_probe", "lbw_batch_step",
+           "lbw_set_populations", "lbw_step_count", "lbw_destroy", "lbw_last_error", "lbw_source",
+           "lbw_batch_create", "lbw_batch_init", "lbw_batch_probe", "lbw_batch_step", "lbw_batch_source",
            "lbw_batch_probe_read", "lbw_batch_spectrum", "lbw_batch_get_populations",
            "lbw_batch_tune", "lbw_batch_info", "lbw_batch_destroy",
            "lbw_mlp_create", "lbw_mlp_param_count", "lbw_mlp_get_params", "lbw_mlp_set_params",
@@ -68,6 +68,8 @@ def lib():
                 "lbw_init": (st, [vp, ctypes.POINTER(lbw_pulse), i32]),
                 "lbw_step": (st, [vp, i64]),
                 "lbw_probe": (st, [vp, ip, i32, i64]),
+                "lbw_source": (st, [vp, ip, i32, i32, ctypes.c_double, ctypes.c_double]),
+                "lbw_batch_source": (st, [vp, ip, i32, i32, ctypes.c_double, dp]),
                 "lbw_probe_read": (st, [vp, dp, i64, ctypes.POINTER(i64)]),
                 "lbw_spectrum": (st, [vp, i32, i32, dp, dp, ip]),
                 "lbw_spectrum_series": (st, [dp, i64, i32, i32, vp, dp, dp, ip]),
@@ -175,6 +177,11 @@ def lbw_probe(grid, q, capacity):
     _check(lib().lbw_probe(grid, _ip(q), q.shape[0], int(capacity)))
 
 
+def lbw_source(grid, q, kind, amp, omega):
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.int32).reshape(-1, 3))
+    _check(lib().lbw_source(grid, _ip(q), q.shape[0], int(kind), float(amp), float(omega)))
+
+
 def lbw_probe_read(grid, n_probes, cap):
     out = np.zeros((max(1, n_probes), max(1, cap)))
     n = ctypes.c_int64()
@@ -274,6 +281,9 @@ class Grid:
     def step(self, n):
         lbw_step(self._h, n)
 
+    def set_sources(self, q, kind=0, amp=1.0, omega=0.0):
+        lbw_source(self._h, q, kind, amp, omega)
+
     def set_probes(self, q, cap):
         q = np.asarray(q, dtype=np.int32).reshape(-1, 3)
         lbw_probe(self._h, q, cap)
@@ -350,6 +360,12 @@ class Batch:
         q = np.ascontiguousarray(np.asarray(q, np.int32).reshape(self.n, -1, 3))
         _check(lib().lbw_batch_probe(self._h, _ip(q), q.shape[1], int(cap)))
         self._per, self._cap = q.shape[1], int(cap)
+
+    def set_sources(self, q, omegas, kind=0, amp=1.0):
+        """q: n x per_member x 3 source nodes; omegas: one angular frequency per member."""
+        q = np.ascontiguousarray(np.asarray(q, np.int32).reshape(self.n, -1, 3))
+        om = np.ascontiguousarray(np.asarray(omegas, np.float64).reshape(self.n))
+        _check(lib().lbw_batch_source(self._h, _ip(q), q.shape[1], int(kind), float(amp), _dp(om)))
 
     def step(self, n):
         _check(lib().lbw_batch_step(self._h, int(n)))

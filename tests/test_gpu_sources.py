@@ -1,0 +1,117 @@
+"""Harmonic sources (the paper's ring / plate sources) on the device against the FP64 oracle,
+single lattices and ensembles, and the resonance sweep built on them."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from lbw_workloads import (BC_BOUNCE, BC_PERIODIC, KIND_CYLINDRICAL, PREC_F32, PREC_F64, GridSpec,
+                           ensemble, pulses, probes)
+from test_gpu_parity import SPECS
+
+pytestmark = pytest.mark.gpu
+
+
+def _ring(spec, q1, q3):
+    return [[q1, j, q3] for j in range(spec.n[1])]
+
+
+def _plate(spec, q3):
+    return [[i, j, q3] for i in range(spec.n[0]) for j in range(spec.n[1])]
+
+
+@pytest.mark.parametrize("prec,tol", [(PREC_F64, 1e-11), (PREC_F32, 2e-5)], ids=["f64", "f32"])
+@pytest.mark.parametrize("name", ["cylinder", "cylinder_unstaged", "cylinder_wide"])
+@pytest.mark.parametrize("kind", [0, 1], ids=["P", "Jz"])
+def test_sources_match_oracle(name, kind, prec, tol):
+    from paper_1705_01801_gb300 import lbw
+    spec = SPECS[name].with_(prec=prec)
+    src = _ring(spec, 0, 2) if kind == 0 else _plate(spec, 0)
+    pl = pulses(spec, 5, 1, sigma=2.5, margin=2)
+    pr = probes(spec, 5, 4, margin=0)
+    g = lbw.Grid(spec)
+    g.init(pl)
+    g.set_sources(src, kind=kind, amp=0.8, omega=0.21)
+    g.set_probes(pr, 130)
+    o = oracle.OracleGrid(spec)
+    o.init(pl)
+    o.set_sources(src, kind=kind, amp=0.8, omega=0.21)
+    o.set_probes(pr, 130)
+    g.step(130)  # 64-step graph chains and single launches both carry the sources
+    o.step(130)
+    fo = o.get_f()
+    np.testing.assert_allclose(g.get_f(), fo, rtol=0, atol=tol * np.abs(fo).max())
+    so = o.read_probes()
+    np.testing.assert_allclose(g.read_probes(), so, rtol=0, atol=tol * 10 * np.abs(so).max())
+
+
+def test_removing_sources_restores_the_free_run():
+    from paper_1705_01801_gb300 import lbw
+    spec = SPECS["cylinder"].with_(prec=PREC_F64)
+    pl = pulses(spec, 6, 1, sigma=2.5, margin=2)
+    a, b = lbw.Grid(spec), lbw.Grid(spec)
+    a.init(pl)
+    b.init(pl)
+    b.set_sources(_ring(spec, 0, 2), omega=0.3)
+    b.set_sources([])
+    a.step(70)
+    b.step(70)
+    np.testing.assert_array_equal(a.get_f(), b.get_f())
+
+
+@pytest.mark.parametrize("prec,tol", [(PREC_F64, 1e-11), (PREC_F32, 2e-5)], ids=["f64", "f32"])
+def test_ensemble_sources_per_member_frequency(prec, tol):
+    """One frequency per member; a source next to the periodic wrap exercises the ghost
+    copies of the padded rows."""
+    from paper_1705_01801_gb300 import lbw
+    specs, _ = ensemble(4, seed=12, r_range=(9, 15), theta_range=(33, 70), z_range=(18, 30), prec=prec)
+    omegas = [0.05, 0.11, 0.17, 0.23]
+    src = [[[2, 0, 1], [2, s.n[1] - 1, 1], [3, s.n[1] // 2, 1]] for s in specs]
+    b = lbw.Batch(specs)
+    b.init([np.zeros((0, 5))] * len(specs))
+    b.set_sources(np.array(src), omegas, kind=0, amp=1.0)
+    b.step(90)
+    for m, s in enumerate(specs):
+        o = oracle.OracleGrid(s)
+        o.init(np.zeros((0, 5)))
+        o.set_sources(src[m], kind=0, amp=1.0, omega=omegas[m])
+        o.step(90)
+        fo = o.get_f()
+        np.testing.assert_allclose(b.get_f(m), fo, rtol=0, atol=tol * np.abs(fo).max())
+
+
+def test_resonance_sweep_finds_the_driven_pipe_mode():
+    """The paper's protocol (Sec. IV.A: a pipe driven by a ring in front of its end, damping D
+    at the walls, the steady-state response at a probe against the source frequency): in a
+    closed pipe the axisymmetric axial modes sit at omega_n = n pi c / L (closed form; a
+    free-decay run of the same lattice finds them with the spectrum estimator), and the
+    sweep's response peak must fall on the measured mode within 1%."""
+    from paper_1705_01801_gb300 import lbw, sweep
+    from lbw_workloads import embedding, node_coords
+    n_r, n_t, n_z = 6, 8, 100
+    c = 0.4
+    spec = GridSpec(kind=KIND_CYLINDRICAL, n=(n_r, n_t, n_z), h=(1, 2 * math.pi / n_t, 1),
+                    x0=(2, 0, 0), c=c, damping=0.98,
+                    bc=(BC_BOUNCE, BC_BOUNCE, BC_PERIODIC, BC_PERIODIC, BC_BOUNCE, BC_BOUNCE),
+                    prec=PREC_F32)
+    ring = _ring(spec, 0, 0)
+    probe = [2, 0, n_z // 10]
+    g = lbw.Grid(spec)
+    pl = []
+    for j in range(n_t):
+        X = embedding(spec, *node_coords(spec, 1, j, 1))
+        pl.append([X[0], X[1], X[2], 1.5, 1.0])
+    g.init(pl)
+    g.set_probes([probe], 8000)
+    g.step(8000)
+    f, _ = g.spectrum(0, 8)
+    theory = 2 * math.pi * c / n_z  # n = 2
+    mode = f[np.argmin(np.abs(f - theory))]
+    assert abs(mode - theory) < 2e-3 * theory
+    omegas = np.linspace(mode * 0.85, mode * 1.15, 41)
+    resp = sweep.resonance_curve(spec, ring, probe, omegas, steps=8000, tail=2000)
+    peak = sweep.peak_frequency(omegas, resp)
+    print(f"closed form {theory:.6f}, free-decay mode {mode:.6f}, sweep peak {peak:.6f} rad/step")
+    assert abs(peak - mode) < 0.01 * mode
+    assert resp.max() > 2 * resp.min()
