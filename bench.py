@@ -281,10 +281,38 @@ def run_ensemble(args):
     }
     if sequential is not None:
         line["vs_sequential"] = sequential
+    if args.surrogate > 0:
+        line["surrogate"] = surrogate_report(specs, args.surrogate)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def surrogate_report(specs, steps):
+    """Mode targets of every member from the batched LBM (steps time steps), a 4-layer 256-wide
+    MLP trained on the first 80% of the members (device kernels, FP32), BF16-weight inference
+    on the rest: held-out mean relative error of the lowest 8 mode frequencies, the error of
+    predicting the training mean, and the per-geometry time of both."""
+    from paper_1705_01801_gb300 import surrogate as S
+    freqs, valid, lbm_s = S.measure(specs, steps=steps, tune=True)
+    X = np.stack([S.features(s) for s in specs])[valid]
+    Y = freqs[valid]
+    ntr = int(0.8 * len(X))
+    sur = S.Surrogate(hidden=256, depth=4, seed=0)
+    sur.fit(X[:ntr], Y[:ntr], steps=4000, batch=32, lr=1e-3)
+    t0 = time.perf_counter()
+    pred = sur.predict(X[ntr:])
+    sur_s = time.perf_counter() - t0
+    err = np.abs(pred - Y[ntr:]) / Y[ntr:]
+    base = np.abs(np.exp(np.log(Y[:ntr]).mean(0)) - Y[ntr:]) / Y[ntr:]
+    return {"members": len(specs), "valid": int(valid.sum()), "time_steps": steps,
+            "held_out": int(len(X) - ntr), "mean_rel_err": float(err.mean()),
+            "mean_rel_err_per_mode": [round(float(x), 4) for x in err.mean(0)],
+            "mean_predictor_rel_err": float(base.mean()),
+            "lbm_s_per_geometry": lbm_s / len(specs),
+            "surrogate_s_per_geometry": sur_s / max(1, len(X) - ntr),
+            "speedup": (lbm_s / len(specs)) / (sur_s / max(1, len(X) - ntr))}
 
 
 def run_reference(args):
@@ -349,6 +377,10 @@ def main():
                     choices=["cylinder", "disk", "trumpet", "torus", "ensemble"])
     ap.add_argument("--members", type=int, default=512,
                     help="ensemble members (--workload ensemble)")
+    ap.add_argument("--surrogate", type=int, default=0, metavar="T",
+                    help="ensemble: measure every member's spectrum over T time steps, train the "
+                         "MLP surrogate on 80%% of the members and report its held-out error and "
+                         "speed against the ensemble run")
     ap.add_argument("--vs-sequential", type=int, default=0, metavar="M",
                     help="ensemble: also time the first M members advanced one after another as "
                          "single lattices (the plain path) and report both rates")
