@@ -1,0 +1,47 @@
+"""Host-side helpers that need no GPU: the sweep's peak refinement and the surrogate's
+geometry features."""
+import math
+
+import numpy as np
+import pytest
+
+import lbw_workloads as W
+
+
+def test_peak_frequency_refines_a_sampled_resonance():
+    from paper_1705_01801_gb300 import sweep
+    w0, gamma = 0.0251, 0.0004
+    omegas = np.linspace(0.8 * w0, 1.2 * w0, 41)
+    resp = 1.0 / np.sqrt((omegas ** 2 - w0 ** 2) ** 2 + (gamma * omegas) ** 2)  # driven oscillator
+    peak = sweep.peak_frequency(omegas, resp)
+    step = omegas[1] - omegas[0]
+    assert abs(peak - w0) < 0.1 * step
+    # a maximum on the edge of the band is returned as is
+    assert sweep.peak_frequency(omegas[:10], resp[:10]) == omegas[9]
+
+
+def test_surrogate_features_of_a_member():
+    from paper_1705_01801_gb300 import surrogate as S
+    n_r, n_t, n_z = 40, 64, 256
+    a0, b, al = W.trumpet_params(3, n_r, n_z)
+    spec = W.ensemble_member(n_r, n_t, n_z, a0, b, al)
+    f = S.features(spec)
+    r_in = spec.x0[0]
+    R = r_in + n_r
+    assert f.shape == (len(S.FEATURE_NAMES),)
+    assert f[0] == pytest.approx(R / 100.0)
+    assert f[1] == pytest.approx(n_z / 512.0)
+    assert f[2] == pytest.approx((a0 + b * math.exp(al * n_z)) / (a0 + b), rel=1e-6)
+    assert f[4] == pytest.approx(n_t / 96.0)
+    assert f[5] == pytest.approx(r_in / R)
+
+
+def test_ensemble_excitation_is_axisymmetric_and_inside():
+    specs, _ = W.ensemble(6, seed=4)
+    for s in specs:
+        pulses, probes = W.ensemble_excitation(s)
+        assert pulses.shape == (12, 5)
+        radii = np.hypot(pulses[:, 0], pulses[:, 1])
+        assert np.ptp(radii) < 1e-9 * radii.max()  # one ring
+        assert (probes >= 0).all() and (probes < np.array(s.n)).all()
+        assert len({tuple(p[[0, 2]]) for p in probes}) == 1  # one corner ring of probes
