@@ -219,6 +219,13 @@ lbw_status lbw_batch_probe_read(lbw_batch* b, double* host_out, int64_t* n_steps
 lbw_status lbw_batch_spectrum(lbw_batch* b, int32_t k, double* host_freq, double* host_amp,
                               int32_t* host_n_found);
 
+/* As lbw_batch_spectrum, but the k LOWEST-frequency peaks of each member's summed series
+ * whose power is at least rel_power (0 < rel_power <= 1) of that member's strongest peak,
+ * sorted by frequency: the lowest modes of a large lattice, which its strongest peaks miss
+ * when hundreds of modes share the band. */
+lbw_status lbw_batch_spectrum_lowest(lbw_batch* b, int32_t k, double rel_power, double* host_freq,
+                                     double* host_amp, int32_t* host_n_found);
+
 /* Member's populations as doubles (7 x N of that member). */
 lbw_status lbw_batch_get_populations(lbw_batch* b, int32_t member, double* host_f);
 

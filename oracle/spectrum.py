@@ -31,8 +31,10 @@ def _dtft_power(xw: np.ndarray, omega: float) -> float:
     return re * re + im * im
 
 
-def spectrum(x, k: int = 8, pad: int = 4, thresh: float = 1e-3, iters: int = 40):
-    """Return (freq[n_found], amp[n_found]) of the k strongest spectral peaks of x."""
+def spectrum(x, k: int = 8, pad: int = 4, thresh: float = 1e-3, iters: int = 40,
+             lowest: bool = False):
+    """Return (freq[n_found], amp[n_found]) of the k strongest spectral peaks of x, or with
+    `lowest` of the k lowest-frequency peaks whose power is at least thresh of the largest."""
     x = np.asarray(x, dtype=np.float64)
     T = x.size
     if T < 4:
@@ -50,7 +52,7 @@ def spectrum(x, k: int = 8, pad: int = 4, thresh: float = 1e-3, iters: int = 40)
         return np.zeros(0), np.zeros(0)
     cand = [j for j in range(1, M // 2)
             if P[j] > P[j - 1] and P[j] >= P[j + 1] and P[j] >= thresh * pmax]
-    cand.sort(key=lambda j: (-P[j], j))
+    cand.sort(key=(lambda j: j) if lowest else (lambda j: (-P[j], j)))
     cand = sorted(cand[:k])
     sw = w.sum()
     freqs, amps = [], []

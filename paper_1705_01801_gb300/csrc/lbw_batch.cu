@@ -1102,6 +1102,25 @@ lbw_status lbw_batch_spectrum(lbw_batch* b, int32_t k, double* host_freq, double
   return LBW_OK;
 }
 
+lbw_status lbw_batch_spectrum_lowest(lbw_batch* b, int32_t k, double rel_power, double* host_freq,
+                                     double* host_amp, int32_t* host_n_found) {
+  if (!b || !host_freq || !host_amp || !host_n_found) return fail(LBW_EINVAL, "NULL argument");
+  if (k < 1 || k > 64) return fail(LBW_EINVAL, "1 <= k <= 64");
+  if (!(rel_power > 0.0 && rel_power <= 1.0)) return fail(LBW_EINVAL, "0 < rel_power <= 1");
+  if (b->nprobe == 0) return fail(LBW_ESTATE, "no probes registered");
+  unsigned long long rec = 0;
+  lbw_status st0 = batch_counters(b, &rec);
+  if (st0 != LBW_OK) return st0;
+  if (rec < 4) return fail(LBW_ESTATE, "fewer than 4 recorded samples");
+  for (int m = 0; m < b->n; ++m) {
+    lbw_status st = spectrum_device(b->series + (size_t)m * b->nprobe * b->cap, (int64_t)rec, b->nprobe,
+                                    (int32_t)b->cap, true, k, b->stream, host_freq + (size_t)m * k,
+                                    host_amp + (size_t)m * k, host_n_found + m, true, rel_power);
+    if (st != LBW_OK) return st;
+  }
+  return LBW_OK;
+}
+
 lbw_status lbw_batch_get_populations(lbw_batch* b, int32_t member, double* host_f) {
   if (!b || !host_f) return fail(LBW_EINVAL, "NULL argument");
   if (member < 0 || member >= b->n) return fail(LBW_EINVAL, "member out of range");

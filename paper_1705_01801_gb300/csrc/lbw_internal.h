@@ -116,8 +116,11 @@ bool encode_tiled_map(void* map, int prec, int rank, void* base, const uint64_t*
                       const uint64_t* strides, const uint32_t* box);
 
 // spectrum (lbw_spectrum.cu) ----------------------------------------------------------------
+// The k strongest peaks (lowest = false) or the k lowest-frequency peaks (lowest = true)
+// whose power is at least rel_power of the strongest.
 lbw_status spectrum_device(const double* d_x, int64_t T, int32_t n_series, int32_t stride_series,
                            bool sum_all, int32_t k, cudaStream_t s, double* h_freq,
-                           double* h_amp, int32_t* h_n);
+                           double* h_amp, int32_t* h_n, bool lowest = false,
+                           double rel_power = 1e-3);
 
 }  // namespace lbw

@@ -133,10 +133,17 @@ __device__ __forceinline__ bool better(double pa, long long ja, double pb, long 
   return pa > pb || (pa == pb && ja < jb);
 }
 
-// k rounds of a block-wide arg-max over the candidate list (warp shuffles), then sort
+// lowest-frequency selection: the lower bin wins
+__device__ __forceinline__ bool lower(double, long long ja, double, long long jb) { return ja < jb; }
+
+// k rounds of a block-wide arg-max over the candidate list (warp shuffles), then sort; the
+// winner of a round is the strongest candidate, or with `lowest` the lowest-frequency one
 __global__ void select_kernel(const double* __restrict__ P, long long* cand,
                               const unsigned long long* __restrict__ count, int k,
-                              long long* chosen, int* n_chosen) {
+                              long long* chosen, int* n_chosen, bool lowest) {
+  auto wins = [&](double pa, long long ja, double pb, long long jb) {
+    return lowest ? lower(pa, ja, pb, jb) : better(pa, ja, pb, jb);
+  };
   __shared__ double sp[32];
   __shared__ long long sj[32];
   __shared__ long long pick[64];
@@ -148,12 +155,12 @@ __global__ void select_kernel(const double* __restrict__ P, long long* cand,
     for (long long i = threadIdx.x; i < n; i += blockDim.x) {
       const long long j = cand[i];
       if (j < 0) continue;
-      if (bj < 0 || better(P[j], j, bp, bj)) { bp = P[j]; bj = j; }
+      if (bj < 0 || wins(P[j], j, bp, bj)) { bp = P[j]; bj = j; }
     }
     for (int o = 16; o > 0; o >>= 1) {
       const double op = __shfl_down_sync(0xffffffffu, bp, o);
       const long long oj = __shfl_down_sync(0xffffffffu, bj, o);
-      if (oj >= 0 && (bj < 0 || better(op, oj, bp, bj))) { bp = op; bj = oj; }
+      if (oj >= 0 && (bj < 0 || wins(op, oj, bp, bj))) { bp = op; bj = oj; }
     }
     if ((threadIdx.x & 31) == 0) { sp[threadIdx.x >> 5] = bp; sj[threadIdx.x >> 5] = bj; }
     __syncthreads();
@@ -163,7 +170,7 @@ __global__ void select_kernel(const double* __restrict__ P, long long* cand,
       for (int o = 16; o > 0; o >>= 1) {
         const double op = __shfl_down_sync(0xffffffffu, bp, o);
         const long long oj = __shfl_down_sync(0xffffffffu, bj, o);
-        if (oj >= 0 && (bj < 0 || better(op, oj, bp, bj))) { bp = op; bj = oj; }
+        if (oj >= 0 && (bj < 0 || wins(op, oj, bp, bj))) { bp = op; bj = oj; }
       }
       if (threadIdx.x == 0) sj[0] = bj;
     }
@@ -246,7 +253,7 @@ __global__ void refine_kernel(const double* __restrict__ xw, long long T, const 
 
 lbw_status spectrum_device(const double* d_x, int64_t T, int32_t n_series, int32_t stride_series,
                            bool sum_all, int32_t k, cudaStream_t s, double* h_freq,
-                           double* h_amp, int32_t* h_n) {
+                           double* h_amp, int32_t* h_n, bool lowest, double rel_power) {
   const int nser = sum_all ? n_series : 1;
   long long M = 1;
   while (M < 4 * T) M <<= 1;
@@ -283,8 +290,8 @@ lbw_status spectrum_device(const double* d_x, int64_t T, int32_t n_series, int32
     }
     power_kernel<<<blocks, 256, 0, s>>>(in, M, P);
     max_kernel<<<1, 1024, 0, s>>>(P, M, stats);
-    candidates_kernel<<<blocks, 256, 0, s>>>(P, M, stats, 1e-3, cand, count);
-    select_kernel<<<1, 1024, 0, s>>>(P, cand, count, k, chosen, n_chosen);
+    candidates_kernel<<<blocks, 256, 0, s>>>(P, M, stats, rel_power, cand, count);
+    select_kernel<<<1, 1024, 0, s>>>(P, cand, count, k, chosen, n_chosen, lowest);
     refine_kernel<<<k, kThreads, 0, s>>>(xw, T, P, M, chosen, n_chosen, stats, freq, amp);
     e = cudaGetLastError();
   }
@@ -391,7 +398,7 @@ extern "C" lbw_status lbw_spectrum_series_static(const double* dev_x, int64_t T,
     power_kernel<<<blocks, 256, 0, s>>>(in, M, P);
     max_kernel<<<1, 1024, 0, s>>>(P, M, stats);
     candidates_kernel<<<blocks, 256, 0, s>>>(P, M, stats, 1e-3, cand, count);
-    select_kernel<<<1, 1024, 0, s>>>(P, cand, count, k, chosen, n_chosen);
+    select_kernel<<<1, 1024, 0, s>>>(P, cand, count, k, chosen, n_chosen, false);
     refine_kernel<<<k, kThreads, 0, s>>>(xw, T, P, M, chosen, n_chosen, stats, freq, amp);
     e = cudaGetLastError();
   }

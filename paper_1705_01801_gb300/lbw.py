@@ -23,7 +23,7 @@ EXPORTS = ["lbw_create_grid", "lbw_init", "lbw_step", "lbw_probe", "lbw_probe_re
            "lbw_spectrum", "lbw_spectrum_series", "lbw_spectrum_series_static", "lbw_get_field", "lbw_get_populations",
            "lbw_set_populations", "lbw_step_count", "lbw_destroy", "lbw_last_error", "lbw_source",
            "lbw_batch_create", "lbw_batch_init", "lbw_batch_probe", "lbw_batch_step", "lbw_batch_source",
-           "lbw_batch_probe_read", "lbw_batch_spectrum", "lbw_batch_get_populations",
+           "lbw_batch_probe_read", "lbw_batch_spectrum", "lbw_batch_spectrum_lowest", "lbw_batch_get_populations",
            "lbw_batch_tune", "lbw_batch_info", "lbw_batch_destroy",
            "lbw_mlp_create", "lbw_mlp_param_count", "lbw_mlp_get_params", "lbw_mlp_set_params",
            "lbw_mlp_forward", "lbw_mlp_predict_bf16", "lbw_mlp_grad", "lbw_mlp_adam_step",
@@ -86,6 +86,7 @@ def lib():
                 "lbw_batch_step": (st, [vp, i64]),
                 "lbw_batch_probe_read": (st, [vp, dp, ctypes.POINTER(i64)]),
                 "lbw_batch_spectrum": (st, [vp, i32, dp, dp, ip]),
+                "lbw_batch_spectrum_lowest": (st, [vp, i32, ctypes.c_double, dp, dp, ip]),
                 "lbw_batch_get_populations": (st, [vp, i32, dp]),
                 "lbw_batch_tune": (st, [vp, i32, ctypes.c_char_p, ctypes.c_char_p, i32]),
                 "lbw_batch_info": (st, [vp, ctypes.POINTER(i64), ip, ip, ip]),
@@ -376,11 +377,16 @@ class Batch:
         _check(lib().lbw_batch_probe_read(self._h, _dp(out), ctypes.byref(n)))
         return out[:, : self._per, : n.value]
 
-    def spectrum(self, k=8):
+    def spectrum(self, k=8, lowest=False, rel_power=1e-3):
+        """Per member the k strongest peaks, or (lowest) the k lowest-frequency peaks with at
+        least rel_power of the strongest's power; frequencies sorted, rad / step."""
         f = np.zeros((self.n, k))
         a = np.zeros((self.n, k))
         c = np.zeros(self.n, np.int32)
-        _check(lib().lbw_batch_spectrum(self._h, int(k), _dp(f), _dp(a), _ip(c)))
+        if lowest:
+            _check(lib().lbw_batch_spectrum_lowest(self._h, int(k), float(rel_power), _dp(f), _dp(a), _ip(c)))
+        else:
+            _check(lib().lbw_batch_spectrum(self._h, int(k), _dp(f), _dp(a), _ip(c)))
         return f, a, c
 
     def get_f(self, member):

@@ -2,8 +2,8 @@
 
 The batched lattice-Boltzmann ensemble (lbw_batch_*) measures, for every member, the spectrum
 of the sum of its probes (a ring of pulses at one rigid corner, a ring of probes at the other,
-so the axisymmetric modes dominate); the lowest `n_modes` frequencies among its strongest
-peaks are the targets.  A multilayer perceptron (lbw_mlp_*: device forward / backward / Adam
+so the axisymmetric modes dominate); its `n_modes` lowest-frequency peaks above a power
+threshold are the targets.  A multilayer perceptron (lbw_mlp_*: device forward / backward / Adam
 kernels, BF16-weight inference) maps normalised geometry features to those frequencies.  The
 lattice-Boltzmann runs remain the judge: `measure` gives the reference values the surrogate
 is trained on and checked against.  All arithmetic runs in the library's kernels; this module
@@ -36,12 +36,11 @@ def features(spec: W.GridSpec) -> np.ndarray:
                     dtype=np.float32)
 
 
-def measure(specs, steps: int, k_strong: int = 24, n_modes: int = 8, rel_amp: float = 0.05,
-            tune: bool = True):
+def measure(specs, steps: int, n_modes: int = 8, rel_power: float = 1e-2, tune: bool = True):
     """Run the ensemble for `steps` time steps and return (freqs [n, n_modes], valid [n],
-    seconds of device work).  Targets are the lowest n_modes frequencies (rad / step) among the
-    k_strong strongest spectral peaks whose amplitude is at least rel_amp of the strongest
-    (window side lobes stay below it); members with fewer such peaks are marked invalid."""
+    seconds of device work).  Targets are the n_modes lowest-frequency spectral peaks (rad /
+    step) whose power is at least rel_power of the member's strongest peak (window side lobes
+    stay below it); members with fewer such peaks are marked invalid."""
     import torch
     b = lbw.Batch(specs)
     if tune:
@@ -52,18 +51,10 @@ def measure(specs, steps: int, k_strong: int = 24, n_modes: int = 8, rel_amp: fl
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.step(steps)
-    f, a, cnt = b.spectrum(k_strong)
+    f, a, cnt = b.spectrum(n_modes, lowest=True, rel_power=rel_power)
     seconds = time.perf_counter() - t0
-    out = np.zeros((len(specs), n_modes))
-    valid = np.zeros(len(specs), bool)
-    for m in range(len(specs)):
-        fm, am = f[m, : cnt[m]], a[m, : cnt[m]]
-        if fm.size == 0:
-            continue
-        fm = np.sort(fm[am >= rel_amp * am.max()])
-        if fm.size >= n_modes:
-            out[m] = fm[:n_modes]
-            valid[m] = True
+    valid = cnt >= n_modes
+    out = np.where(valid[:, None], f, 0.0)
     b.close()
     return out, valid, seconds
 

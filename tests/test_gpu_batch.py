@@ -150,3 +150,23 @@ def test_sixteen_bit_members_error_bound(prec, unit):
         fo, fg = o.get_f(), b.get_f(m)
         rel = np.linalg.norm(fg - fo) / np.linalg.norm(fo)
         assert rel <= 3 * unit * math.sqrt(steps), (m, rel)
+
+
+def test_lowest_peaks_match_oracle_estimator():
+    """lbw_batch_spectrum_lowest against the oracle estimator's lowest-frequency selection."""
+    from paper_1705_01801_gb300 import lbw
+    specs = _small_ensemble(PREC_F64, n=3)
+    exc = [ensemble_excitation(s, sigma=2.5) for s in specs]
+    b = lbw.Batch(specs)
+    b.init([e[0] for e in exc])
+    b.set_probes(np.stack([e[1] for e in exc]), 1500)
+    b.step(1500)
+    f, a, cnt = b.spectrum(5, lowest=True, rel_power=1e-2)
+    for m, s in enumerate(specs):
+        o = oracle.OracleGrid(s)
+        o.init(exc[m][0])
+        o.set_probes(exc[m][1], 1500)
+        o.step(1500)
+        fo, _ = oracle.spectrum(o.read_probes().sum(0), 5, thresh=1e-2, lowest=True)
+        assert cnt[m] == len(fo)
+        np.testing.assert_allclose(f[m, : cnt[m]], fo, rtol=1e-8)

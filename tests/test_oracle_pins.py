@@ -530,3 +530,19 @@ def test_spectrum_synthetic_sinusoids():
     fr, am = oracle.spectrum(x, 3)
     np.testing.assert_allclose(fr, om, rtol=0, atol=1e-7)  # 1e-4 of a DFT bin
     np.testing.assert_allclose(am, amp, rtol=2e-2)
+
+
+def test_spectrum_lowest_selection():
+    """With `lowest` the estimator returns the lowest-frequency components above the power
+    threshold, in order, even when stronger components sit higher in the band; components
+    below the threshold are left out."""
+    t = np.arange(6000)
+    om = np.array([0.0101, 0.0233, 0.0387, 0.2210, 0.3501])
+    amp = np.array([0.3, 0.2, 0.04, 1.0, 0.9])  # 0.04^2 = 1.6e-3 of the largest power
+    x = sum(a * np.cos(w * t + p) for a, w, p in zip(amp, om, (0.2, 0.9, 1.7, 2.5, 0.4)))
+    fr, _ = oracle.spectrum(x, 2, thresh=1e-2, lowest=True)
+    np.testing.assert_allclose(fr, om[:2], rtol=0, atol=1e-6)
+    fr, _ = oracle.spectrum(x, 3, thresh=1e-2, lowest=True)
+    np.testing.assert_allclose(fr, [om[0], om[1], om[3]], rtol=0, atol=1e-6)  # 0.0387 is too weak
+    fr, _ = oracle.spectrum(x, 2)  # the default picks the strongest
+    np.testing.assert_allclose(fr, om[3:], rtol=0, atol=1e-6)
