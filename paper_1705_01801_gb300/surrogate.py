@@ -36,7 +36,7 @@ def features(spec: W.GridSpec) -> np.ndarray:
                     dtype=np.float32)
 
 
-def measure(specs, steps: int, n_modes: int = 8, rel_power: float = 1e-2, tune: bool = True):
+def measure(specs, steps: int, n_modes: int = 8, rel_power: float = 1e-3, tune: bool = True):
     """Run the ensemble for `steps` time steps and return (freqs [n, n_modes], valid [n],
     seconds of device work).  Targets are the n_modes lowest-frequency spectral peaks (rad /
     step) whose power is at least rel_power of the member's strongest peak (window side lobes
