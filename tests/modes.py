@@ -34,3 +34,17 @@ def annulus_wavenumbers(m, a, R, count=3):
 def pipe_zeros(m, count=3):
     f = lambda x: (m + 1) * jv(m, x) - x * jv(m + 1, x)
     return roots(f, 1e-3, 30.0)[:count]
+
+
+def bessel_horn_wavenumbers(lam, z_a, z_b, count=4):
+    """Axial wavenumbers of Webster's horn equation (the plane-wave limit of the wave equation
+    in a duct) for the paper's Bessel horn, cross-section area S ~ s^2 = Zc^(-2 lam) with
+    Zc = Zmax - z, between rigid ends at Zc = z_a and Zc = z_b (dP/dz = 0).  In Zc the
+    equation P'' - (2 lam / Zc) P' + k^2 P = 0 has the solutions Zc^nu C_nu(k Zc) with
+    nu = lam + 1/2 (C a cylinder function), whose derivative is k Zc^nu C_(nu-1)(k Zc);
+    rigid ends therefore need J_(nu-1)(k z_a) Y_(nu-1)(k z_b) - Y_(nu-1)(k z_a) J_(nu-1)(k z_b)
+    = 0.  lam = 0 gives the pipe, k = n pi / (z_b - z_a)."""
+    o = lam - 0.5
+    f = lambda k: jv(o, k * z_a) * yv(o, k * z_b) - yv(o, k * z_a) * jv(o, k * z_b)
+    span = z_b - z_a
+    return roots(f, 1e-3 / span, (count + 1.5) * np.pi / span)[:count]

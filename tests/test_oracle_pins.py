@@ -14,8 +14,8 @@ import pytest
 import oracle
 from lbw_workloads import (BC_ANTIBOUNCE, BC_BOUNCE, BC_FREE, BC_PERIODIC, KIND_CARTESIAN,
                            KIND_CYLINDRICAL, KIND_POLAR, KIND_TOROIDAL, KIND_TRUMPET,
-                           PROFILE_BESSEL, PROFILE_EXP, GridSpec, embedding)
-from modes import annulus_radial, annulus_wavenumbers, pipe_zeros
+                           PROFILE_BESSEL, PROFILE_EXP, GridSpec, bessel_horn, embedding)
+from modes import annulus_radial, annulus_wavenumbers, bessel_horn_wavenumbers, pipe_zeros
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 W = lambda cs2: np.array([1 - 3 * cs2] + [cs2 / 2] * 6)
@@ -322,6 +322,44 @@ def test_paper_pipe_zeros_golden():
     assert ours[0] == pytest.approx(printed[0], abs=3e-4)
     assert ours[1] == pytest.approx(printed[1], abs=3e-4)
     assert abs(ours[2] - printed[2]) > 1e-2 and ours[2] == pytest.approx(7.1558, abs=1e-4)
+
+
+def _axial_modes(spec, steps=8000, count=4):
+    """Lowest axial mode frequencies of a free run from a radially uniform Gaussian in z."""
+    n1, n2, n3 = spec.n
+    g = oracle.OracleGrid(spec)
+    z = np.arange(n3) + 0.5
+    Pz = np.exp(-0.5 * ((z - 0.15 * n3) / 3.0) ** 2)
+    sg = np.array([[g.geometry(q1, 0, q3)[0] for q1 in range(n1)] for q3 in range(n3)])
+    g.set_f(state_from_rho(sg[:, :, None] * Pz[:, None, None] * np.ones(n2)))
+    g.set_probes([[n1 // 2, 0, 2]], steps)
+    g.step(steps)
+    from oracle.spectrum import spectrum
+    f, _ = spectrum(g.read_probes()[0], k=count, lowest=True, thresh=1e-3)
+    assert len(f) == count
+    return np.asarray(f)
+
+
+def test_bessel_horn_axial_modes_follow_webster():
+    """Sec. IV.B pipe-versus-horn comparison: the axial modes of a thin Bessel horn with rigid
+    ends follow Webster's horn equation (Zc^nu C_nu(k Zc), nu = lam + 1/2).  The lattice's own
+    dispersion cancels in the ratio to the same lattice's pipe (lam = 0, omega = n pi c / L);
+    that ratio must match Webster's k_horn / (n pi / L) within 1e-3 for the four lowest modes
+    (the flare lowers the fundamental by 2-3.5%).  A dropped or sign-flipped g^{rz} coupling
+    moves it by 3-10%."""
+    pipe_spec = bessel_horn(0.0)
+    L = pipe_spec.n[2]
+    pipe = _axial_modes(pipe_spec)
+    n_pi_L = np.arange(1, 5) * math.pi / L
+    assert np.all(np.abs(pipe / (pipe_spec.c * n_pi_L) - 1) < 2e-3)
+    for lam in (0.2, 0.4):
+        spec = bessel_horn(lam)
+        zmax = spec.geom[0]
+        k = np.asarray(bessel_horn_wavenumbers(lam, zmax - L, zmax, 4))
+        horn = _axial_modes(spec)
+        shift_lbm, shift_webster = horn / pipe, k / n_pi_L
+        assert shift_webster[0] < 0.98
+        assert np.all(np.abs(shift_lbm - shift_webster) < 1e-3), (lam, shift_lbm, shift_webster)
 
 
 # ---------------------------------------------------------------- finite differences ------
