@@ -143,6 +143,13 @@ lbw_status lbw_probe_read(lbw_grid* g, double* host_out, int64_t cap_per_probe,
 lbw_status lbw_spectrum(lbw_grid* g, int32_t probe, int32_t k, double* host_freq,
                         double* host_amp, int32_t* n_found);
 
+/* As lbw_spectrum, but the k LOWEST-frequency peaks whose power is at least rel_power
+ * (0 < rel_power <= 1) of the strongest peak, sorted by frequency: the lowest normal modes
+ * (the pipe-versus-horn comparison of Sec. IV.B), which the strongest peaks miss when many
+ * modes share the band.  LBW_EINVAL for rel_power outside (0, 1]. */
+lbw_status lbw_spectrum_lowest(lbw_grid* g, int32_t probe, int32_t k, double rel_power,
+                               double* host_freq, double* host_amp, int32_t* n_found);
+
 /* The same estimator on caller-provided series: host_x = n_series x T doubles. */
 lbw_status lbw_spectrum_series(const double* host_x, int64_t T, int32_t n_series, int32_t k,
                                void* stream, double* host_freq, double* host_amp,

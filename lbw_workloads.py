@@ -102,13 +102,14 @@ def bessel_horn(lam: float, n=(3, 4, 64), z_gap: float = 12.0, c: float = WAVE_S
                 prec=PREC_F64) -> GridSpec:
     """The paper's Bessel horn s = (Zmax - z)^-lam over 0 < z < n3, Zmax = n3 + z_gap, rigid
     walls and rigid ends (lam = 0 is the straight pipe).  The radial spacing h_r = 1 / s_min
-    keeps the physical cell at least one unit wide where the horn is narrowest, and r_in keeps
-    the azimuthal lattice speed c / (r s h_theta) <= KAPPA_THETA there."""
+    keeps the physical cell at least one unit wide where the horn is narrowest; r_in keeps the
+    azimuthal lattice speed c / (r s h_theta) <= KAPPA_THETA there and the ghost node half a
+    cell inside the inner wall at r > 0."""
     n1, n2, n3 = n
     zmax = n3 + z_gap
     s_min = zmax ** -lam
     h_r = 1.0 / s_min
-    r_in = max(1.0, math.ceil(c / (KAPPA_THETA * s_min * 2 * math.pi / n2) - 0.5 * h_r))
+    r_in = float(max(math.ceil(h_r), math.ceil(c / (KAPPA_THETA * s_min * 2 * math.pi / n2) - 0.5 * h_r)))
     return GridSpec(kind=KIND_TRUMPET, n=tuple(n), h=(h_r, 2 * math.pi / n2, 1.0),
                     x0=(r_in, 0.0, 0.0), c=c, geom=(zmax, lam, 0.0, 0.0), profile=PROFILE_BESSEL,
                     bc=(BC_BOUNCE, BC_BOUNCE, BC_PERIODIC, BC_PERIODIC, BC_BOUNCE, BC_BOUNCE),

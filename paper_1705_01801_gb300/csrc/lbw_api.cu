@@ -517,6 +517,21 @@ lbw_status lbw_spectrum(lbw_grid* g, int32_t probe, int32_t k, double* host_freq
                          probe < 0, k, g->stream, host_freq, host_amp, n_found);
 }
 
+lbw_status lbw_spectrum_lowest(lbw_grid* g, int32_t probe, int32_t k, double rel_power,
+                               double* host_freq, double* host_amp, int32_t* n_found) {
+  if (!g || !host_freq || !host_amp || !n_found) return fail(LBW_EINVAL, "NULL argument");
+  if (probe < -1 || probe >= g->nprobe) return fail(LBW_EINVAL, "probe index out of range");
+  if (k < 1 || k > 64) return fail(LBW_EINVAL, "1 <= k <= 64");
+  if (!(rel_power > 0.0 && rel_power <= 1.0)) return fail(LBW_EINVAL, "0 < rel_power <= 1");
+  unsigned long long rec = 0;
+  lbw_status st = read_counters(g, &rec);
+  if (st != LBW_OK) return st;
+  if (rec < 4) return fail(LBW_ESTATE, "fewer than 4 recorded samples");
+  const double* base = g->series + (probe >= 0 ? (size_t)probe * g->cap : 0);
+  return spectrum_device(base, (int64_t)rec, probe >= 0 ? 1 : g->nprobe, (int32_t)g->cap,
+                         probe < 0, k, g->stream, host_freq, host_amp, n_found, true, rel_power);
+}
+
 lbw_status lbw_spectrum_series(const double* host_x, int64_t T, int32_t n_series, int32_t k,
                                void* stream, double* host_freq, double* host_amp,
                                int32_t* host_n_found) {

@@ -20,7 +20,7 @@ STATUS_NAMES = ["LBW_OK", "LBW_EINVAL", "LBW_ENOMEM", "LBW_ECUDA", "LBW_EUNSTABL
 
 # every symbol the header declares (checked by tests/test_abi.py)
 EXPORTS = ["lbw_create_grid", "lbw_init", "lbw_step", "lbw_probe", "lbw_probe_read",
-           "lbw_spectrum", "lbw_spectrum_series", "lbw_spectrum_series_static", "lbw_get_field", "lbw_get_populations",
+           "lbw_spectrum", "lbw_spectrum_lowest", "lbw_spectrum_series", "lbw_spectrum_series_static", "lbw_get_field", "lbw_get_populations",
            "lbw_set_populations", "lbw_step_count", "lbw_destroy", "lbw_last_error", "lbw_source",
            "lbw_batch_create", "lbw_batch_init", "lbw_batch_probe", "lbw_batch_step", "lbw_batch_source",
            "lbw_batch_probe_read", "lbw_batch_spectrum", "lbw_batch_spectrum_lowest", "lbw_batch_get_populations",
@@ -72,6 +72,7 @@ def lib():
                 "lbw_batch_source": (st, [vp, ip, i32, i32, ctypes.c_double, dp]),
                 "lbw_probe_read": (st, [vp, dp, i64, ctypes.POINTER(i64)]),
                 "lbw_spectrum": (st, [vp, i32, i32, dp, dp, ip]),
+                "lbw_spectrum_lowest": (st, [vp, i32, i32, ctypes.c_double, dp, dp, ip]),
                 "lbw_spectrum_series": (st, [dp, i64, i32, i32, vp, dp, dp, ip]),
                 "lbw_spectrum_series_static": (st, [vp, i64, i32, vp, dp, dp, ip]),
                 "lbw_get_field": (st, [vp, dp]),
@@ -198,6 +199,15 @@ def lbw_spectrum(grid, probe, k):
     return f[: n.value], a[: n.value]
 
 
+def lbw_spectrum_lowest(grid, probe, k, rel_power=1e-3):
+    f = np.zeros(k)
+    a = np.zeros(k)
+    n = ctypes.c_int32()
+    _check(lib().lbw_spectrum_lowest(grid, int(probe), int(k), float(rel_power), _dp(f), _dp(a),
+                                     ctypes.byref(n)))
+    return f[: n.value], a[: n.value]
+
+
 def lbw_spectrum_series(x, k, stream=None):
     x = np.ascontiguousarray(np.atleast_2d(np.asarray(x, dtype=np.float64)))
     ns, T = x.shape
@@ -293,7 +303,11 @@ class Grid:
     def read_probes(self):
         return lbw_probe_read(self._h, self._nprobe, self._cap)
 
-    def spectrum(self, probe=0, k=8):
+    def spectrum(self, probe=0, k=8, lowest=False, rel_power=1e-3):
+        """k strongest peaks, or with `lowest` the k lowest-frequency peaks whose power is at
+        least rel_power of the strongest; (freq rad/step, amp), sorted by frequency."""
+        if lowest:
+            return lbw_spectrum_lowest(self._h, probe, k, rel_power)
         return lbw_spectrum(self._h, probe, k)
 
     def get_P(self):
