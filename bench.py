@@ -270,7 +270,9 @@ def run_ensemble(args):
                    "l2": f"working set {2 * 7 * nodes * elem / 1e9:.1f} GB vs 129 MB L2",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "ensemble step kernel",
+                     "frac": achieved / peak,
+                     "traffic": profiled_ensemble_traffic(nodes) if prec == W.PREC_F32 else None,
+                     "kernel": "ensemble step kernel",
                      "peak_source": peak_kind, "bytes_per_node": 14 * elem,
                      "kernel_us": kernel_ms * 1e3},
         "cpu_baseline": base,
@@ -569,28 +571,51 @@ def f64_deviation(lbw, wl, lbm_steps, grid, stream_handle, k=8):
 
 
 PROFILE = os.path.join(ROOT, "profiles", "step_tma_kernel_cylinder_128x128x256_f32.md")
+ENSEMBLE_PROFILE = os.path.join(ROOT, "profiles", "batch_tma_kernel_ensemble_32_trumpets_f32.md")
+
+
+def source_hash(name):
+    import hashlib
+    p = os.path.join(ROOT, "paper_1705_01801_gb300", "csrc", name)
+    with open(p, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 def lbw_kernel_hash():
-    import hashlib
-    p = os.path.join(ROOT, "paper_1705_01801_gb300", "csrc", "lbw_step.cu")
-    with open(p, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    return source_hash("lbw_step.cu")
+
+
+def _profile_fields(path):
+    fields = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and not line.startswith(("#", "|", " ")):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+    return fields
 
 
 def profiled_traffic():
     """DRAM bytes per launch of the step kernel from the committed ncu summary, or None when
     the kernel source changed since the counters were taken."""
     try:
-        fields = {}
-        with open(PROFILE) as fh:
-            for line in fh:
-                if ":" in line and not line.startswith(("#", "|", " ")):
-                    k, v = line.split(":", 1)
-                    fields[k.strip()] = v.strip()
+        fields = _profile_fields(PROFILE)
         if fields.get("step_source_sha256_16") != lbw_kernel_hash():
             return None
         return int(fields["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def profiled_ensemble_traffic(nodes):
+    """DRAM bytes per launch of the FP32 ensemble kernel: the committed ncu summary's bytes per
+    node (a 32-member capture of the same member distribution) times the ensemble's nodes, or
+    None when the ensemble source changed since the counters were taken."""
+    try:
+        fields = _profile_fields(ENSEMBLE_PROFILE)
+        if fields.get("batch_source_sha256_16") != source_hash("lbw_batch.cu"):
+            return None
+        return int(round(float(fields["traffic_bytes_per_node"]) * nodes))
     except Exception:
         return None
 
