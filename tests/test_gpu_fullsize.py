@@ -1,0 +1,77 @@
+"""Parity at the benchmark workloads' full sizes, in the launch configuration the benchmark
+times: the 256 x 256 x 512 trumpet (FP32 and FP16 storage), the 192 x 1024 x 256 torus (FP32
+and BF16 storage) and the 512-trumpet ensemble.  One device step from a shared state against
+one FP64 oracle step, every node compared; the ensemble on sampled members."""
+import numpy as np
+import pytest
+
+import lbw_workloads as W
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+W_D3Q7 = np.array([0.25] + [0.125] * 6)  # weights at cs^2 = 1/4
+
+
+def _shared_state(spec, seed):
+    """Random populations (7, N3, N1, N2) that the storage type holds exactly: FP32 values,
+    or w_i h_i with h_i = k / 64, |k| <= 64, for the 16-bit forms (they store h_i = f_i / w_i;
+    k / 64 needs at most 7 significand bits)."""
+    rng = np.random.default_rng(seed)
+    shape = (7, spec.n[2], spec.n[0], spec.n[1])
+    if spec.prec == W.PREC_F32:
+        return rng.standard_normal(shape, dtype=np.float32).astype(np.float64)
+    h = rng.integers(-64, 65, size=shape).astype(np.float64) / 64.0
+    return h * W_D3Q7[:, None, None, None]
+
+
+# storage rounding of one step's result: half an ulp of FP32 (with the FP32 arithmetic),
+# FP16 (11 significand bits) and BF16 (8)
+RTOL = {W.PREC_F32: 0.0, W.PREC_F16S: 2.0 ** -11, W.PREC_BF16S: 2.0 ** -8}
+
+
+@pytest.mark.parametrize("name,prec", [("trumpet", W.PREC_F32), ("trumpet", W.PREC_F16S),
+                                       ("torus", W.PREC_F32), ("torus", W.PREC_BF16S)],
+                         ids=["trumpet-f32", "trumpet-f16", "torus-f32", "torus-bf16"])
+def test_one_step_full_size(name, prec):
+    from paper_1705_01801_gb300 import lbw
+    spec = {"trumpet": W.trumpet, "torus": W.torus}[name](prec=prec)
+    f = _shared_state(spec, seed=11)
+    g = lbw.Grid(spec)
+    try:
+        g.set_f(f)
+        g.step(1)
+        fg = g.get_f()
+    finally:
+        g.close()
+    o = oracle.OracleGrid(spec)
+    o.set_f(f)
+    del f
+    o.step(1)
+    fo = o.get_f()
+    o.close()
+    scale = np.abs(fo).max()
+    np.testing.assert_allclose(fg, fo, rtol=RTOL[prec], atol=1e-6 * scale)
+
+
+def test_ensemble_full_size_sampled_members():
+    """The 512-trumpet ensemble with the autotuned launch shape, three steps from the
+    benchmark's excitation; members 0, 255 and 511 against the oracle run of each member."""
+    from paper_1705_01801_gb300 import lbw
+    specs, _ = W.ensemble(512, seed=5)
+    exc = [W.ensemble_excitation(s) for s in specs]
+    b = lbw.Batch(specs)
+    try:
+        b.tune(trial_steps=2)
+        b.init([e[0] for e in exc])
+        b.step(3)
+        got = {m: b.get_f(m) for m in (0, 255, 511)}
+    finally:
+        b.close()
+    for m, fg in got.items():
+        o = oracle.OracleGrid(specs[m])
+        o.init(exc[m][0])
+        o.step(3)
+        fo = o.get_f()
+        o.close()
+        np.testing.assert_allclose(fg, fo, rtol=0, atol=2e-5 * np.abs(fo).max())
