@@ -111,6 +111,9 @@ __global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
   constexpr int TABB = ((BY * T_SLOTS * RS) + 127) / 128 * 128;
   constexpr int RHOB = ((3 * PS * RS) + 127) / 128 * 128;
   constexpr bool SC = Store<S>::kScaled;
+  // slot grouping as in step_tma_kernel: 32- and 64-bit storage carry population 6 of plane
+  // p + 1 in plane p's slot, 16-bit storage keeps whole planes
+  constexpr bool RG = sizeof(S) >= 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) StepArgs<S> A;
   __shared__ int probe_list[kMaxProbes];
@@ -192,21 +195,28 @@ __global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         const unsigned tx_pop = (unsigned)(ROWS * RW * ES);
         int s = 0, use = 0, issued = z0 - 3;
-        for (int p = z0 - 2; p <= z1 + 1; ++p) {
+        for (int p = z0 - 2; p <= z1 + (RG ? 0 : 1); ++p) {
           if (use > 0 && !wait_bar(empty_at(s), (unsigned)((use - 1) & 1))) break;
           const unsigned bar = full_at(s);
           const unsigned base = sbase + SL + s * SLOTB;
           const int pg = resolve(p, A.n3, p3);
-          if (pg < 0) {
-            mbar_expect_tx(bar, 0);
-          } else if (p == z0 - 2) {  // only population 5 of this plane streams into the segment
-            mbar_expect_tx(bar, tx_pop);
-            tma_load_4d(base + 5 * POPB, tm_f, x0, y0 - 1, pg, 5, bar);
+          if (p == z0 - 2) {
+            // only population 5 of this plane streams into the segment; when the first pulled
+            // plane z0 - 1 is the q3 = 0 face of a wall, its reflected population 6 rides here
+            const int pn = (RG && !p3 && z0 == 1) ? 0 : -1;
+            mbar_expect_tx(bar, (pg < 0 ? 0u : tx_pop) + (pn >= 0 ? tx_pop : 0u));
+            if (pg >= 0) tma_load_4d(base + 5 * POPB, tm_f, x0, y0 - 1, pg, 5, bar);
+            if (pn >= 0) tma_load_4d(base + 6 * POPB, tm_f, x0, y0 - 1, pn, 6, bar);
           } else {
-            const bool tab = p >= z0 && p < z1;
-            mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
+            const int pn = RG ? resolve(p + 1, A.n3, p3) : pg;
+            const bool tab = pg >= 0 && p >= z0 && p < z1;
+            mbar_expect_tx(bar, (pg >= 0 ? 6 * tx_pop : 0u) + (pn >= 0 ? tx_pop : 0u) +
+                                    (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
 #pragma unroll 1
-            for (int i = 0; i < 7; ++i) tma_load_4d(base + i * POPB, tm_f, x0, y0 - 1 - xi1_of(i), pg, i, bar);
+            for (int i = 0; i < 7; ++i) {
+              const int pi = i == 6 ? pn : pg;
+              if (pi >= 0) tma_load_4d(base + i * POPB, tm_f, x0, y0 - 1 - xi1_of(i), pi, i, bar);
+            }
             if (tab) tma_load_3d(sbase + TAB + s * TABB, tm_t, 0, y0, pg, bar);
           }
           issued = p;
@@ -243,8 +253,8 @@ __global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
         else { o2 = POPB + own + RW * ES; m2 = wall(b); }
       }
       const unsigned o3e = 3 * POPB + own - ES, o4e = 4 * POPB + own + NPT * ES;
-      const unsigned f5_face = (A.bc[4] == LBW_BC_FREE ? 5 : 6) * POPB;
-      const unsigned f6_face = (A.bc[5] == LBW_BC_FREE ? 6 : 5) * POPB;
+      const bool f5_own = A.bc[4] == LBW_BC_FREE, f6_own = A.bc[5] == LBW_BC_FREE;
+      const unsigned f5_face = (f5_own ? 5 : 6) * POPB, f6_face = (f6_own ? 6 : 5) * POPB;
       const R m5_face = A.bc[4] == LBW_BC_FREE ? R(1) : wall(A.bc[4]);
       const R m6_face = A.bc[5] == LBW_BC_FREE ? R(1) : wall(A.bc[5]);
 
@@ -295,9 +305,15 @@ __global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
                        bool wr) {
         const bool zlo = !p3 && u == 0, zhi = !p3 && u == A.n3 - 1;
         const bool zghost = !p3 && (u < 0 || u >= A.n3);
-        const unsigned S0 = SL + sl0 * SLOTB;
-        const unsigned B5 = zlo ? S0 + f5_face : SL + slm * SLOTB + 5 * POPB;
-        const unsigned B6 = zhi ? S0 + f6_face : SL + slp * SLOTB + 6 * POPB;
+        const unsigned S0 = SL + sl0 * SLOTB, SM = SL + slm * SLOTB;
+        unsigned B5, B6;
+        if constexpr (RG) {  // slot sl0: pops 0-5 of u, pop 6 of u + 1; slm: pop 6 of u
+          B5 = zlo ? (f5_own ? S0 + 5 * POPB : SM + 6 * POPB) : SM + 5 * POPB;
+          B6 = zhi ? (f6_own ? SM + 6 * POPB : S0 + 5 * POPB) : S0 + 6 * POPB;
+        } else {
+          B5 = zlo ? S0 + f5_face : SM + 5 * POPB;
+          B6 = zhi ? S0 + f6_face : SL + slp * SLOTB + 6 * POPB;
+        }
         const R m5 = zlo ? m5_face : R(1), m6 = zhi ? m6_face : R(1);
         R t3[NPT], t4[NPT];
         ldv(S0 + own, f[0]);
@@ -454,25 +470,26 @@ __global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
         }
       };
 
-      bool ok = wait_bar(full_at(0), 0) && wait_bar(full_at(1), 0) && wait_bar(full_at(2), 0);
+      constexpr int AHEAD = RG ? 0 : 1;
+      bool ok = wait_bar(full_at(0), 0) && wait_bar(full_at(1), 0) && (RG || wait_bar(full_at(2), 0));
       if (ok && owner) stepA(z0 - 1, fB, rA, 0, 1, 2, 2, false);
       if (lane == 0) mbar_arrive(empty_at(0));
-      ok = ok && wait_bar(full_at(3), 0);
+      ok = ok && wait_bar(full_at(2 + AHEAD), 0);
       if (ok) stepA(z0, fA, rB, 1, 2, 3, 0, true);
       if (lane == 0) mbar_arrive(empty_at(1));
       ok = !named_sync_or(1, NCW * 32, !ok || abort_flag);
-      int sz = 2, s1 = 3, s2 = 4, u2 = 0, rbz = 0, rb1 = 1;
+      int sz = 2, s1 = 3, s2 = 4, uw = 0, rbz = 0, rb1 = 1;
       auto advance = [&]() {
         rbz = rb1;
         rb1 = rb1 == 2 ? 0 : rb1 + 1;
         sz = s1;
         s1 = s2;
         s2 = s2 == NB - 1 ? 0 : s2 + 1;
-        if (s2 == 0) ++u2;
+        if ((RG ? s1 : s2) == 0) ++uw;
       };
       auto iter = [&](int zz, R (&fc)[7][NPT], R (&fn)[7][NPT], const R (&rp)[NPT],
                       const R (&rc)[NPT], R (&rn)[NPT], bool collide) {
-        const bool in = wait_bar(full_at(s2), (unsigned)(u2 & 1));
+        const bool in = wait_bar(full_at(RG ? s1 : s2), (unsigned)(uw & 1));
         if (in) stepA(zz + 1, fn, rn, sz, s1, s2, rb1, true);
         const bool go = !named_sync_or(1, NCW * 32, !in || abort_flag);
         if (go && collide) stepB(zz, fc, rp, rc, rn, sz, rbz);

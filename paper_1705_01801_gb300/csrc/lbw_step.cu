@@ -74,9 +74,14 @@ struct TmaLayout {
 // population a main box of BX columns x BY + 2 rows (rows shifted by the population's xi1, so
 // the pull of tile row w reads staged row w of every population) and two V-column halo
 // boxes at x0 - V and x0 + BX (periodic wraps in the coordinates), plus the tile's
-// coefficient rows; the plane below the segment carries population 5 only.  The slot's full
-// mbarrier completes on the bytes, and a slot is refilled only after every consumer warp has
-// released it (empty mbarrier), so the producer runs up to NB - 3 planes ahead.  Per plane u
+// coefficient rows.  With 32- or 64-bit storage a slot holds populations 0-5 of its plane
+// and population 6 of the next one (the population that streams down into the plane), so
+// pulling plane u needs the slots of planes u and u - 1 only and the last slot is plane z1;
+// with 16-bit storage a slot holds its whole plane, pulling plane u needs planes u - 1 .. u + 1
+// and the last slot is plane z1 + 1.  The plane below the segment carries population 5 only.
+// The slot's full mbarrier completes on the bytes, and a slot is refilled only after every
+// consumer warp has released it (empty mbarrier), so the producer runs up to NB - 2 (16-bit:
+// NB - 3) planes ahead.  Per plane u
 // the consumers pull their populations and write rho into one of three rotating rho planes
 // (step A), synchronise among themselves (named barrier) and collide plane u - 1 (step B,
 // rows of the tile only).  Face rules are reads of other staged values (bounce-back /
@@ -91,6 +96,10 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_tab) {
   using R = typename Store<S>::R;
   constexpr int BX = 32 * NPT, NB = 5, ROWS = BY + 2, NCW = ROWS;  // consumer warps
+  // 32- and 64-bit storage: population 6 of plane p + 1 rides in plane p's slot (measured:
+  // FP32 trumpet 6% and cylinder 2% faster); 16-bit storage keeps whole planes per slot (the
+  // regrouped form measured 7-8% slower there)
+  constexpr bool RG = sizeof(S) >= 4;
   constexpr int ES = (int)sizeof(S), RS = (int)sizeof(R);
   constexpr int V = 16 / ES;
   constexpr int MB = TmaLayout<BY, BX>::template main_bytes<S>();
@@ -165,25 +174,55 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       const unsigned tx_pop = (unsigned)(ROWS * BX * ES) + (hl ? ROWS * 16u : 0u) + (hr ? ROWS * 16u : 0u);
       int s = 0, use = 0;
       int issued = z0 - 3;
-      for (int p = z0 - 2; p <= z1 + 1; ++p) {
+      for (int p = z0 - 2; p <= z1 + (RG ? 0 : 1); ++p) {
         if (use > 0 && !wait_bar(empty_at(s), (unsigned)((use - 1) & 1))) break;
         const unsigned bar = full_at(s);
         const unsigned base = sbase + SL + s * SLOTB;
         const int pg = resolve(p, a.n3, p3);
-        if (pg < 0) {
-          mbar_expect_tx(bar, 0);
-        } else if (p == z0 - 2) {  // only population 5 of this plane streams into the segment
-          mbar_expect_tx(bar, (unsigned)(ROWS * BX * ES));
-          tma_load_4d(base + 5 * POPB, &tm_main, x0, y0 - 1, pg, 5, bar);
+        if constexpr (!RG) {  // whole planes
+          if (pg < 0) {
+            mbar_expect_tx(bar, 0);
+          } else if (p == z0 - 2) {  // only population 5 of this plane streams into the segment
+            mbar_expect_tx(bar, (unsigned)(ROWS * BX * ES));
+            tma_load_4d(base + 5 * POPB, &tm_main, x0, y0 - 1, pg, 5, bar);
+          } else {
+            const bool tab = p >= z0 && p < z1;
+            mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
+#pragma unroll 1
+            for (int i = 0; i < 7; ++i) {
+              const int row = y0 - 1 - xi1_of(i);
+              tma_load_4d(base + i * POPB, &tm_main, x0, row, pg, i, bar);
+              if (hl) tma_load_4d(base + i * POPB + MB, &tm_halo, xl, row, pg, i, bar);
+              if (hr) tma_load_4d(base + i * POPB + MB + HB, &tm_halo, xr, row, pg, i, bar);
+            }
+            if (tab) tma_load_3d(sbase + TAB + s * TABB, &tm_tab, 0, y0, pg, bar);
+          }
+        } else if (p == z0 - 2) {
+          // only population 5 of this plane streams into the segment; when the first pulled
+          // plane z0 - 1 is the q3 = 0 face of a wall, its reflected population 6 rides here
+          const int pn = (!p3 && z0 == 1) ? 0 : -1;
+          mbar_expect_tx(bar, (pg < 0 ? 0u : (unsigned)(ROWS * BX * ES)) + (pn >= 0 ? tx_pop : 0u));
+          if (pg >= 0) tma_load_4d(base + 5 * POPB, &tm_main, x0, y0 - 1, pg, 5, bar);
+          if (pn >= 0) {
+            tma_load_4d(base + 6 * POPB, &tm_main, x0, y0 - 1, pn, 6, bar);
+            if (hl) tma_load_4d(base + 6 * POPB + MB, &tm_halo, xl, y0 - 1, pn, 6, bar);
+            if (hr) tma_load_4d(base + 6 * POPB + MB + HB, &tm_halo, xr, y0 - 1, pn, 6, bar);
+          }
         } else {
-          const bool tab = p >= z0 && p < z1;
-          mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
+          // populations 0-5 of plane p and population 6 of plane p + 1 (which streams into
+          // plane p), so a pulled plane needs its own slot and the one before it only
+          const int pn = resolve(p + 1, a.n3, p3);
+          const bool tab = pg >= 0 && p >= z0 && p < z1;
+          mbar_expect_tx(bar, (pg >= 0 ? 6 * tx_pop : 0u) + (pn >= 0 ? tx_pop : 0u) +
+                                  (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
 #pragma unroll 1
           for (int i = 0; i < 7; ++i) {
+            const int pi = i == 6 ? pn : pg;
+            if (pi < 0) continue;
             const int row = y0 - 1 - xi1_of(i);
-            tma_load_4d(base + i * POPB, &tm_main, x0, row, pg, i, bar);
-            if (hl) tma_load_4d(base + i * POPB + MB, &tm_halo, xl, row, pg, i, bar);
-            if (hr) tma_load_4d(base + i * POPB + MB + HB, &tm_halo, xr, row, pg, i, bar);
+            tma_load_4d(base + i * POPB, &tm_main, x0, row, pi, i, bar);
+            if (hl) tma_load_4d(base + i * POPB + MB, &tm_halo, xl, row, pi, i, bar);
+            if (hr) tma_load_4d(base + i * POPB + MB + HB, &tm_halo, xr, row, pi, i, bar);
           }
           if (tab) tma_load_3d(sbase + TAB + s * TABB, &tm_tab, 0, y0, pg, bar);
         }
@@ -236,9 +275,10 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     // q2 faces (non-periodic q2): free copies the node's own value, walls reflect the opposite
     const bool q2lo_free = a.bc[2] == LBW_BC_FREE, q2hi_free = a.bc[3] == LBW_BC_FREE;
     const R q2lo_m = sc1 * wall(a.bc[2]), q2hi_m = sc1 * wall(a.bc[3]);
-    // q3 faces: slot offset and factor of populations 5 / 6 at the first / last plane
-    const unsigned f5_face = (a.bc[4] == LBW_BC_FREE ? 5 : 6) * POPB;
-    const unsigned f6_face = (a.bc[5] == LBW_BC_FREE ? 6 : 5) * POPB;
+    // q3 faces: populations 5 / 6 at the first / last plane take the node's own value (free)
+    // or its opposite population (walls), with these factors
+    const bool f5_own = a.bc[4] == LBW_BC_FREE, f6_own = a.bc[5] == LBW_BC_FREE;
+    const unsigned f5_face = (f5_own ? 5 : 6) * POPB, f6_face = (f6_own ? 6 : 5) * POPB;
     const R m5_face = a.bc[4] == LBW_BC_FREE ? sc1 : sc1 * wall(a.bc[4]);
     const R m6_face = a.bc[5] == LBW_BC_FREE ? sc1 : sc1 * wall(a.bc[5]);
 
@@ -286,13 +326,23 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     S* const dst_z0 = a.fout + node(owner ? q1 : 0, q2, z0, a.n1, a.n2);
 
     // step A of pulled plane u: populations into f, rho into rr and (wr) the rho plane
+    // slots of planes u - 1, u, u + 1.  Regrouped (RG): slot sl0 holds populations 0-5 of
+    // plane u and population 6 of plane u + 1, slot slm population 5 of plane u - 1 and
+    // population 6 of plane u (the faces' own values), slot slp is not read.  Otherwise each
+    // slot holds its whole plane.
     auto stepA = [&](int u, R (&f)[7][NPT], R (&rr)[NPT], int slm, int sl0, int slp, int rbu,
                      bool wr) {
       const bool zlo = !p3 && u == 0, zhi = !p3 && u == a.n3 - 1;
       const bool zghost = !p3 && (u < 0 || u >= a.n3);
-      const unsigned S0 = SL + sl0 * SLOTB;
-      const unsigned B5 = zlo ? S0 + f5_face : SL + slm * SLOTB + 5 * POPB;
-      const unsigned B6 = zhi ? S0 + f6_face : SL + slp * SLOTB + 6 * POPB;
+      const unsigned S0 = SL + sl0 * SLOTB, SM = SL + slm * SLOTB;
+      unsigned B5, B6;
+      if constexpr (RG) {
+        B5 = zlo ? (f5_own ? S0 + 5 * POPB : SM + 6 * POPB) : SM + 5 * POPB;
+        B6 = zhi ? (f6_own ? SM + 6 * POPB : S0 + 5 * POPB) : S0 + 6 * POPB;
+      } else {
+        B5 = zlo ? S0 + f5_face : SM + 5 * POPB;
+        B6 = zhi ? S0 + f6_face : SL + slp * SLOTB + 6 * POPB;
+      }
       const R m5 = zlo ? m5_face : sc1, m6 = zhi ? m6_face : sc1;
       R t3[NPT], t4[NPT];
       ldv(S0 + own, f[0]);
@@ -477,32 +527,36 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
 
     // rho of plane z0 - 1 at the own nodes, from the staged planes z0 - 2 (population 5 only),
     // z0 - 1 and z0; then step A of plane z0
-    bool ok = wait_bar(full_at(0), 0) && wait_bar(full_at(1), 0) && wait_bar(full_at(2), 0);
+    // the slot that completes what step A of plane u needs: u's own (RG) or u + 1's
+    constexpr int AHEAD = RG ? 0 : 1;
+    bool ok = wait_bar(full_at(0), 0) && wait_bar(full_at(1), 0) && (RG || wait_bar(full_at(2), 0));
     if (ok && owner) stepA(z0 - 1, fB, rA, 0, 1, 2, 2, false);
     if (lane == 0) mbar_arrive(empty_at(0));  // plane z0 - 2 is no longer needed
-    ok = ok && wait_bar(full_at(3), 0);
+    ok = ok && wait_bar(full_at(2 + AHEAD), 0);
     if (ok) stepA(z0, fA, rB, 1, 2, 3, 0, true);
     if (lane == 0) mbar_arrive(empty_at(1));  // nor is plane z0 - 1
     ok = !named_sync_or(1, NCW * 32, !ok || abort_flag);
     // slots of raw planes z, z + 1, z + 2 (plane z0 - 2 sits in slot 0) and the fill count of
-    // plane z + 2's slot, advanced plane by plane.  rho planes rotate through three buffers: a
-    // warp writing plane z + 1's buffer has passed the barrier that follows every read of that
-    // buffer (plane z - 2); the rows of plane z0 - 1 in buffer 2 are never written or read.
-    int sz = 2, s1 = 3, s2 = 4, u2 = 0, rbz = 0, rb1 = 1;
+    // the awaited slot (plane z + 1's or z + 2's), advanced plane by plane.  rho planes rotate
+    // through three buffers: a warp writing plane z + 1's buffer has passed the barrier that
+    // follows every read of that buffer (plane z - 2); the rows of plane z0 - 1 in buffer 2
+    // are never written or read.
+    int sz = 2, s1 = 3, s2 = 4, uw = 0, rbz = 0, rb1 = 1;
     auto advance = [&]() {
       rbz = rb1;
       rb1 = rb1 == 2 ? 0 : rb1 + 1;
       sz = s1;
       s1 = s2;
       s2 = s2 == NB - 1 ? 0 : s2 + 1;
-      if (s2 == 0) ++u2;
+      if ((RG ? s1 : s2) == 0) ++uw;
     };
-    // iteration z: raw plane z + 2 in, A(z + 1), barrier, B(z), release raw plane z.  Every
-    // warp passes the same barriers; the barrier ORs the warps' abort states (a timed-out wait
-    // here, or the producer's flag), so all warps leave after the same iteration.
+    // iteration z: raw plane z + 1 (RG) or z + 2 in, A(z + 1), barrier, B(z), release raw
+    // plane z.  Every warp passes the same barriers; the barrier ORs the warps' abort states
+    // (a timed-out wait here, or the producer's flag), so all warps leave after the same
+    // iteration.
     auto iter = [&](int zz, R (&fc)[7][NPT], R (&fn)[7][NPT], const R (&rp)[NPT],
                     const R (&rc)[NPT], R (&rn)[NPT], bool collide) {
-      const bool in = wait_bar(full_at(s2), (unsigned)(u2 & 1));
+      const bool in = wait_bar(full_at(RG ? s1 : s2), (unsigned)(uw & 1));
       if (in) stepA(zz + 1, fn, rn, sz, s1, s2, rb1, true);
       const bool go = !named_sync_or(1, NCW * 32, !in || abort_flag);
       if (go && collide) stepB(zz, fc, rp, rc, rn, sz, rbz);
