@@ -253,7 +253,7 @@ void lbw_batch_destroy(lbw_batch* b);
 /* ------------------------------------------------------------------------------------------
  * Surrogate: a multilayer perceptron from ensemble geometry parameters to mode frequencies,
  * trained and evaluated on the device (the paper has no counterpart; the lattice-Boltzmann
- * runs stay the judge of its error).  depth weight layers in -> hidden -> ... -> out, tanh
+ * runs stay the reference for its error).  depth weight layers in -> hidden -> ... -> out, tanh
  * after every layer but the last.  Loss: mean over samples and outputs of (y - t)^2.
  * Parameters: one FP32 vector, per layer W (out x in, row-major) then b (out).  Host arrays
  * are row-major float32 (n x in inputs, n x out targets).

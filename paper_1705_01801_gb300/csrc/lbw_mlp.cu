@@ -1,6 +1,6 @@
 // lbw_mlp.cu -- a small multilayer perceptron, trained and evaluated on the device, used as a
 // surrogate from ensemble geometry parameters to the lowest mode frequencies the batched
-// lattice-Boltzmann runs measure (the paper has no counterpart; the LBM stays the judge).
+// lattice-Boltzmann runs measure (the paper has no counterpart; the LBM stays the reference).
 //
 // Network: depth weight layers, in -> hidden -> ... -> hidden -> out, tanh after every layer
 // but the last (linear).  Loss: mean over samples and outputs of (y - t)^2.  Parameters are one

@@ -5,7 +5,7 @@ of the sum of its probes (a ring of pulses at one rigid corner, a ring of probes
 so the axisymmetric modes dominate); its `n_modes` lowest-frequency peaks above a power
 threshold are the targets.  A multilayer perceptron (lbw_mlp_*: device forward / backward / Adam
 kernels, BF16-weight inference) maps normalised geometry features to those frequencies.  The
-lattice-Boltzmann runs remain the judge: `measure` gives the reference values the surrogate
+lattice-Boltzmann runs remain the reference: `measure` gives the values the surrogate
 is trained on and checked against.  All arithmetic runs in the library's kernels; this module
 only assembles arrays.
 """

@@ -62,7 +62,7 @@ def test_training_fits_a_smooth_map():
     assert loss[-50:].mean() < 0.02 * loss[:10].mean()
 
 
-def test_surrogate_against_ensemble_judge():
+def test_surrogate_against_ensemble():
     """Train on spectra the batched LBM measures for seeded trumpets and check held-out
     members: the surrogate answers in microseconds what the ensemble takes seconds for, at a
     stated mode-frequency error (mean relative, held out)."""
