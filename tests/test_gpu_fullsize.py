@@ -1,7 +1,8 @@
 """Parity at the benchmark workloads' full sizes, in the launch configuration the benchmark
-times: the 256 x 256 x 512 trumpet (FP32 and FP16 storage), the 192 x 1024 x 256 torus (FP32
-and BF16 storage) and the 512-trumpet ensemble.  One device step from a shared state against
-one FP64 oracle step, every node compared; the ensemble on sampled members."""
+times: the 256 x 256 x 512 trumpet (FP32 and FP16 storage) and the 192 x 1024 x 256 torus
+(FP32 and BF16 storage), one device step from a shared state against one FP64 oracle step at
+every node; the 512-trumpet ensemble on sampled members; the 128 x 128 disk over its full
+4000 steps."""
 import numpy as np
 import pytest
 
@@ -75,3 +76,29 @@ def test_ensemble_full_size_sampled_members():
         fo = o.get_f()
         o.close()
         np.testing.assert_allclose(fg, fo, rtol=0, atol=2e-5 * np.abs(fo).max())
+
+
+def test_disk_full_run_matches_oracle():
+    """The 128 x 128 FP64 disk in full: 4000 steps from the benchmark's pulse, the four probe
+    series within 1e-10 of their peak, the final populations within 1e-10 of the oracle's
+    largest, and the spectrum of the summed probes equal to the oracle estimator's."""
+    from paper_1705_01801_gb300 import lbw
+    w = W.workload("disk")
+    g = lbw.Grid(w.spec)
+    o = oracle.OracleGrid(w.spec)
+    try:
+        for grid in (g, o):
+            grid.init(w.pulses)
+            grid.set_probes(w.probes, w.steps)
+            grid.step(w.steps)
+        xg, xo = g.read_probes(), o.read_probes()
+        assert xg.shape == xo.shape == (len(w.probes), w.steps)
+        assert np.abs(xg - xo).max() <= 1e-10 * np.abs(xo).max()
+        fo = o.get_f()
+        np.testing.assert_allclose(g.get_f(), fo, rtol=0, atol=1e-10 * np.abs(fo).max())
+        fg_sum, _ = g.spectrum(-1, 4)
+        fo_sum, _ = oracle.spectrum(xo.sum(0), 4)
+        np.testing.assert_allclose(fg_sum, fo_sum, rtol=1e-8)
+    finally:
+        g.close()
+        o.close()

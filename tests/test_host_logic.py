@@ -1,5 +1,5 @@
-"""Host-side helpers that need no GPU: the sweep's peak refinement and the surrogate's
-geometry features."""
+"""Host-side helpers that need no GPU: the sweep's peak refinement, the surrogate's
+geometry features, the ensemble excitation and the benchmark's profile bookkeeping."""
 import math
 
 import numpy as np
@@ -45,3 +45,21 @@ def test_ensemble_excitation_is_axisymmetric_and_inside():
         assert np.ptp(radii) < 1e-9 * radii.max()  # one ring
         assert (probes >= 0).all() and (probes < np.array(s.n)).all()
         assert len({tuple(p[[0, 2]]) for p in probes}) == 1  # one corner ring of probes
+
+
+def test_profiled_traffic_follows_the_kernel_source(monkeypatch):
+    """bench.py reports ncu DRAM traffic only while the kernel source still hashes to the
+    value recorded with the counters; the ensemble's bytes per node scale with its nodes."""
+    import bench
+    step = bench._profile_fields(bench.PROFILE)
+    ens = bench._profile_fields(bench.ENSEMBLE_PROFILE)
+    real = {"lbw_step.cu": step["step_source_sha256_16"],
+            "lbw_batch.cu": ens["batch_source_sha256_16"]}
+    monkeypatch.setattr(bench, "source_hash", lambda name: real[name])
+    assert bench.profiled_traffic() == int(step["traffic_bytes_per_launch"])
+    per_node = float(ens["traffic_bytes_per_node"])
+    assert bench.profiled_ensemble_traffic(1000) == round(per_node * 1000)
+    monkeypatch.setattr(bench, "source_hash", lambda name: "0" * 16)
+    assert bench.profiled_traffic() is None
+    assert bench.profiled_ensemble_traffic(1000) is None
+
