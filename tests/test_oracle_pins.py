@@ -312,6 +312,34 @@ def test_cylinder_axial_mode():
     assert abs(om / (spec.c * math.hypot(k, math.pi / Nz)) - 1) < 2e-3
 
 
+def test_cylinder_mode_converges_at_second_order():
+    """Sec. IV.A convergence claim in curvilinear coordinates: the (m = 0, radial 0, axial 1)
+    mode of a closed annular cylinder (a = 3, R = 15, L = 16; rigid inner wall, Dirichlet outer
+    wall and caps) resolved with 1, 2 and 4 cells per unit (c per step scaled with the cell)
+    approaches its closed form with error ratios of 4 (order 2; a one-step lag in the
+    neighbour densities would make it order 1)."""
+    a, R, L, c0 = 3.0, 15.0, 16.0, 0.4
+    k = annulus_wavenumbers(0, a, R, 1)[0]
+    errs = []
+    for s in (1, 2, 4):
+        n_r, n_z, n_t = int((R - a) * s), int(L * s), 8
+        spec = GridSpec(kind=KIND_CYLINDRICAL, n=(n_r, n_t, n_z), h=(1 / s, 2 * math.pi / n_t, 1 / s),
+                        x0=(a, 0, 0), c=c0 / s,
+                        bc=(BC_BOUNCE, BC_ANTIBOUNCE, BC_PERIODIC, BC_PERIODIC, BC_ANTIBOUNCE,
+                            BC_ANTIBOUNCE))
+        r = a + (np.arange(n_r) + 0.5) / s
+        z = (np.arange(n_z) + 0.5) / s
+        P0 = np.sin(math.pi * z / L)[:, None, None] * annulus_radial(0, k, a, r)[None, :, None] \
+            * np.ones(n_t)
+        g = oracle.OracleGrid(spec)
+        g.set_f(state_from_rho((r * spec.h[0] * spec.h[1] * spec.h[2])[None, :, None] * P0))
+        g.set_probes([[n_r // 3, 0, n_z // 3]], 1500 * s)
+        g.step(1500 * s)
+        fr, am = oracle.spectrum(g.read_probes()[0], 3)
+        errs.append(abs(fr[np.argmax(am)] / (spec.c * math.hypot(k, math.pi / L)) - 1))
+    assert 3.6 < errs[0] / errs[1] < 4.4 and 3.6 < errs[1] / errs[2] < 4.4, errs
+
+
 def test_paper_pipe_zeros_golden():
     """The printed zeros of (m+1) J_m(x) - x J_{m+1}(x), m = 0 (appendix table): the first
     two are reproduced by the root finder the mode pins use; the third is a misprint."""
