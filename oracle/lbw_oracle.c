@@ -29,9 +29,12 @@
  *      minus sign and with cs^2 (not c^2) in the delta term.  Pinned by the flat-space wave
  *      speed test (c != cs).
  *   R2 the Christoffel term carries sqrt(g) (Eq. 2ConservationcurvedForce): -c^2 rho G^a.
- *      Pinned by the annulus Bessel frequencies.
+ *      Pinned by the annulus Bessel frequencies; the trumpet's assembled metric terms by the
+ *      Bessel horn's axial modes against Webster's horn equation.
  *   R3 D3Q7 weights (the figure is missing): w_0 = 1 - 3 cs^2, w_i = cs^2 / 2, cs^2 a parameter.
  *   R4 neighbour rho for the gradient is taken at the same time level (after streaming).
+ *      Pinned by second-order convergence, in flat space and on an annular cylinder mode (a
+ *      one-step lag would make the scheme first order).
  *   R5 ghost values for the gradient at a non-periodic face: free -> rho copied; bounce-back
  *      (rigid) -> P mirrored (even); anti-bounce-back (Dirichlet) -> P mirrored with a sign
  *      change (odd); the ghost's metric is evaluated at the ghost position.
