@@ -45,3 +45,52 @@ def test_invalid_descriptor_rejected_without_gpu():
     st = lbw.lib().lbw_create_grid(ctypes.byref(desc), None, ctypes.byref(out))
     assert st == lbw.LBW_EINVAL
     assert "tau" in lbw.lbw_last_error()
+
+
+def _desc(**kw):
+    """A valid 8 x 16 x 8 cylinder descriptor with fields overridden by kw."""
+    import math
+    import lbw_workloads as W
+    spec = W.GridSpec(kind=W.KIND_CYLINDRICAL, n=(8, 16, 8), h=(1, 2 * math.pi / 16, 1),
+                      x0=(4, 0, 0), c=0.3,
+                      bc=(W.BC_BOUNCE, W.BC_ANTIBOUNCE, 0, 0, W.BC_BOUNCE, W.BC_BOUNCE))
+    d = lbw.make_desc(spec)
+    for k, v in kw.items():
+        if k == "bc":
+            for i, b in enumerate(v):
+                d.bc[i] = b
+        else:
+            setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("fields,message", [
+    ({"kind": 7}, "kind"),
+    ({"damping": 1.5}, "damping"),
+    ({"prec": 9}, "prec"),
+    ({"bc": (0, 1, 0, 0, 1, 1)}, "pairs"),           # periodic on one q1 face only
+    ({"bc": (1, 2, 1, 1, 1, 1)}, "angular"),         # theta not periodic
+    ({"kind": 3, "horn_profile": 5}, "horn_profile"),
+    ({"c": 1.5}, "too coarse"),                      # beyond the stability bound
+    ({"x0": (-6.0, 0.0, 0.0)}, "metric undefined"),  # r <= 0 on the lattice
+], ids=["kind", "damping", "prec", "periodic-pair", "angular", "horn", "stability", "metric"])
+def test_descriptor_rules_are_checked_on_the_host(fields, message):
+    """Every descriptor rule of lbw_create_grid is decided before any CUDA call: the status is
+    LBW_EINVAL and the thread's last error names the rule."""
+    d = _desc(**fields)
+    out = ctypes.c_void_p()
+    st = lbw.lib().lbw_create_grid(ctypes.byref(d), None, ctypes.byref(out))
+    assert st == lbw.LBW_EINVAL
+    assert message in lbw.lbw_last_error(), lbw.lbw_last_error()
+
+
+def test_valid_descriptor_passes_the_host_checks():
+    """The base descriptor of the rule table satisfies every rule (so each case above fails on
+    its own field): it gets past validation to the first CUDA call, which fails without a GPU
+    (LBW_ECUDA) and succeeds with one."""
+    d = _desc()
+    out = ctypes.c_void_p()
+    st = lbw.lib().lbw_create_grid(ctypes.byref(d), None, ctypes.byref(out))
+    assert st in (lbw.LBW_ECUDA, lbw.LBW_OK), lbw.lbw_last_error()
+    if st == lbw.LBW_OK:
+        lbw.lbw_destroy(out)
