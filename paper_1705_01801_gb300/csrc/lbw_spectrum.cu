@@ -278,6 +278,9 @@ lbw_status spectrum_device(const double* d_x, int64_t T, int32_t n_series, int32
   double* amp = (double*)take(64 * 8);
   (void)p;
 
+  // a launch error left behind by an unrelated earlier runtime call on this thread would
+  // otherwise be read back below as this call's failure
+  (void)cudaGetLastError();
   cudaError_t e = cudaMemsetAsync(count, 0, 8, s);
   const int blocks = 152 * 4;
   if (e == cudaSuccess) {
