@@ -355,7 +355,7 @@ static void apply_sources(OGrid *g, double *f) {
 }
 
 static void one_step(OGrid *g) {
-  const double c2 = g->c * g->c, cs2 = g->cs2;
+  const double cs2 = g->cs2;
   const double w0 = 1.0 - 3.0 * cs2, w1 = 0.5 * cs2;
   /* 1 + 2: stream, then rho = sum_i f_i at every node */
 #pragma omp parallel for schedule(static)
