@@ -38,8 +38,8 @@
  *   R5 ghost values for the gradient at a non-periodic face: free -> rho copied; bounce-back
  *      (rigid) -> P mirrored (even); anti-bounce-back (Dirichlet) -> P mirrored with a sign
  *      change (odd); the ghost's metric is evaluated at the ghost position.  Walls are pinned
- *      by the annulus, closed-pipe and horn modes; the free (copy) face meets no closed form:
- *      parity unpinned for it.
+ *      by the annulus, closed-pipe and horn modes; the free (copy) face only by a uniform
+ *      state staying uniform: it meets no closed form, parity unpinned for its reflection.
  *   R6 the metric is written in lattice coordinates q: x^a = x0^a + (q^a + 1/2) h^a, so
  *      g_q^{ab} = g^{ab} / (h_a h_b), sqrt(g_q) = h1 h2 h3 sqrt(g), G_q^a = G^a / h_a.
  *   R7 initial state at rest: J'(0) = 0 (Eq. JShifted), so the stored post-collision

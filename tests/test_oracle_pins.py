@@ -263,6 +263,26 @@ def test_mass_conservation_torus():
     assert g.get_f().sum() == pytest.approx(m0, rel=1e-12, abs=1e-12)
 
 
+def test_free_faces_keep_a_uniform_state():
+    """Flat space, free (copy) faces on q1 and q3: a uniform state at rest is a steady state
+    (each face pulls the node's own population, and the copied ghost density leaves no
+    gradient), so every population keeps its value; walls and anti-bounce-back faces do not
+    (the latter pull the field towards P = 0).  This fixes the face's own-population copy,
+    not its reflection: the free face meets no closed form beyond this."""
+    bc_free = (BC_FREE, BC_FREE, BC_PERIODIC, BC_PERIODIC, BC_FREE, BC_FREE)
+    spec = GridSpec(kind=KIND_CARTESIAN, n=(6, 5, 7), h=(1, 1, 1), x0=(0, 0, 0), c=0.45,
+                    bc=bc_free)
+    f0 = state_from_rho(np.full((7, 6, 5), 0.8))
+    g = oracle.OracleGrid(spec)
+    g.set_f(f0)
+    g.step(50)
+    np.testing.assert_allclose(g.get_f(), f0, rtol=0, atol=1e-14)
+    d = oracle.OracleGrid(spec.with_(bc=(BC_ANTIBOUNCE,) * 2 + bc_free[2:]))
+    d.set_f(f0)
+    d.step(50)
+    assert np.abs(d.get_f() - f0).max() > 1e-3
+
+
 # ---------------------------------------------------------------- Bessel modes ------------
 
 def _annulus_spec(Nr=32, Nt=128, r_in=8.0, c=0.4, Nz=1, L=None):
