@@ -72,6 +72,18 @@ def test_metric_matches_embedding(spec):
 
 
 @pytest.mark.parametrize("spec", GEOMS, ids=["cart", "cyl", "bessel", "exp", "torus"])
+def test_pulse_placement_uses_the_coordinate_map(spec):
+    """The oracle places Gaussian pulses by the embedding distance; its embedding is the
+    paper's coordinate map (Eqs. cylindricalsystem, coordinatesTrumpet, CoordinatesTorus),
+    the same map whose Jacobian gives the metric pinned above."""
+    rng = np.random.default_rng(7)
+    g = oracle.OracleGrid(spec)
+    for _ in range(20):
+        u = np.array(spec.x0) + rng.uniform(0.5, 3.5, 3) * np.array(spec.h)
+        np.testing.assert_allclose(g.embed(*u), embedding(spec, *u), rtol=1e-13, atol=1e-12)
+
+
+@pytest.mark.parametrize("spec", GEOMS, ids=["cart", "cyl", "bessel", "exp", "torus"])
 def test_contracted_christoffel_identity(spec):
     """G^a = g^{bc} Gamma^a_{bc} = -(1/sqrt g) d_b (sqrt g g^{ab}) (a divergence identity),
     with sqrt g, g^{ab} from the embedding and d_b by central differences."""
