@@ -48,3 +48,23 @@ def bessel_horn_wavenumbers(lam, z_a, z_b, count=4):
     f = lambda k: jv(o, k * z_a) * yv(o, k * z_b) - yv(o, k * z_a) * jv(o, k * z_b)
     span = z_b - z_a
     return roots(f, 1e-3 / span, (count + 1.5) * np.pi / span)[:count]
+
+
+def webster_wavenumbers(s, ds, length, count=4):
+    """Axial wavenumbers of Webster's horn equation P'' + 2 (s'/s) P' + k^2 P = 0 (cross-section
+    area ~ s(z)^2) between rigid ends at z = 0 and z = length (P' = 0), for any flare s(z) with
+    derivative ds(z): shooting from z = 0 with P = 1, P' = 0 and bracketing the roots of P'(length)
+    in k (scipy's adaptive Runge-Kutta at 1e-11 relative tolerance)."""
+    from scipy.integrate import solve_ivp
+
+    def end_slope(k):
+        rhs = lambda z, y: [y[1], -2.0 * ds(z) / s(z) * y[1] - k * k * y[0]]
+        return solve_ivp(rhs, (0.0, length), [1.0, 0.0], rtol=1e-11, atol=1e-12).y[1, -1]
+
+    ks = np.linspace(1e-3 / length, (count + 1.5) * np.pi / length, 60 * (count + 2))
+    v = [end_slope(k) for k in ks]
+    out = []
+    for i in range(len(ks) - 1):
+        if v[i] * v[i + 1] < 0:
+            out.append(brentq(end_slope, ks[i], ks[i + 1], xtol=1e-13))
+    return out[:count]

@@ -15,7 +15,8 @@ import oracle
 from lbw_workloads import (BC_ANTIBOUNCE, BC_BOUNCE, BC_FREE, BC_PERIODIC, KIND_CARTESIAN,
                            KIND_CYLINDRICAL, KIND_POLAR, KIND_TOROIDAL, KIND_TRUMPET,
                            PROFILE_BESSEL, PROFILE_EXP, GridSpec, bessel_horn, embedding)
-from modes import annulus_radial, annulus_wavenumbers, bessel_horn_wavenumbers, pipe_zeros
+from modes import (annulus_radial, annulus_wavenumbers, bessel_horn_wavenumbers, pipe_zeros,
+                   webster_wavenumbers)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 W = lambda cs2: np.array([1 - 3 * cs2] + [cs2 / 2] * 6)
@@ -420,6 +421,40 @@ def test_bessel_horn_axial_modes_follow_webster():
         shift_lbm, shift_webster = horn / pipe, k / n_pi_L
         assert shift_webster[0] < 0.98
         assert np.all(np.abs(shift_lbm - shift_webster) < 1e-3), (lam, shift_lbm, shift_webster)
+
+
+def test_webster_shooting_reproduces_the_bessel_horn():
+    """The shooting solver used for flares without a closed form gives the Bessel horn's
+    wavenumbers (Zc^nu C_nu(k Zc) solutions) to 1e-9."""
+    lam, za, zb = 0.4, 12.0, 76.0
+    s = lambda z: (zb - z) ** -lam
+    ds = lambda z: lam * (zb - z) ** (-lam - 1)
+    np.testing.assert_allclose(webster_wavenumbers(s, ds, zb - za, 4),
+                               bessel_horn_wavenumbers(lam, za, zb, 4), rtol=1e-9)
+
+
+def test_exponential_horn_axial_modes_follow_webster():
+    """The benchmark trumpets' flare a(z) = a0 + b e^(alpha z) (Eq. coordinatesTrumpet with an
+    exponential s(z)): on a thin lattice the four lowest axial modes, as ratios to the same
+    lattice's pipe, match Webster's horn equation solved by shooting within 1.5e-3 (the flare
+    doubles the radius over the length and lowers the fundamental by 3.7%)."""
+    a0, b, alpha = 2.0, 0.2, 0.04
+    n, c = (3, 8, 64), 0.4
+    L = n[2]
+    r_in = float(max(1, math.ceil(c / (2 * math.pi / n[1]) - 0.5)))
+
+    def horn(geom):
+        return GridSpec(kind=KIND_TRUMPET, n=n, h=(1.0, 2 * math.pi / n[1], 1.0), x0=(r_in, 0, 0),
+                        c=c, geom=geom, profile=PROFILE_EXP,
+                        bc=(BC_BOUNCE, BC_BOUNCE, BC_PERIODIC, BC_PERIODIC, BC_BOUNCE, BC_BOUNCE))
+    flared = _axial_modes(horn((a0, b, alpha, 0.0)))
+    pipe = _axial_modes(horn((1.0, 0.0, 0.0, 0.0)))
+    s = lambda z: (a0 + b * math.exp(alpha * z)) / (a0 + b)
+    ds = lambda z: b * alpha * math.exp(alpha * z) / (a0 + b)
+    k = np.asarray(webster_wavenumbers(s, ds, L, 4))
+    ratio_webster = k / (np.arange(1, 5) * math.pi / L)
+    assert ratio_webster[0] < 0.97
+    assert np.all(np.abs(flared / pipe - ratio_webster) < 1.5e-3), (flared / pipe, ratio_webster)
 
 
 # ---------------------------------------------------------------- finite differences ------
