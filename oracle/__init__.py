@@ -35,7 +35,7 @@ PINS = {
     "step/annulus": "Bessel annulus closed form (rigid inner, Dirichlet outer) within 0.2%",
     "step/cylinder": "annulus x sin(n pi z / L) closed form within 0.2%",
     "step/trumpet,torus": "finite-difference solve of the wave equation, order-2 agreement; "
-                          "Bessel-horn axial modes vs Webster's horn equation",
+                          "Bessel and exponential horns' axial modes vs Webster's horn equation",
     "step/linear operator": "spectral radius <= 1 and eigen-angles vs spectrum estimator",
     "spectrum": "synthetic sinusoids with known frequencies",
 }

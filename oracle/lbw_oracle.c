@@ -30,7 +30,7 @@
  *      speed test (c != cs).
  *   R2 the Christoffel term carries sqrt(g) (Eq. 2ConservationcurvedForce): -c^2 rho G^a.
  *      Pinned by the annulus Bessel frequencies; the trumpet's assembled metric terms by the
- *      Bessel horn's axial modes against Webster's horn equation.
+ *      axial modes of Bessel and exponential horns against Webster's horn equation.
  *   R3 D3Q7 weights (the figure is missing): w_0 = 1 - 3 cs^2, w_i = cs^2 / 2, cs^2 a parameter.
  *   R4 neighbour rho for the gradient is taken at the same time level (after streaming).
  *      Pinned by second-order convergence, in flat space and on an annular cylinder mode (a
