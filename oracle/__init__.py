@@ -38,6 +38,13 @@ PINS = {
                           "Bessel and exponential horns' axial modes vs Webster's horn equation",
     "step/linear operator": "spectral radius <= 1 and eigen-angles vs spectrum estimator",
     "spectrum": "synthetic sinusoids with known frequencies",
+    "face/free": "open-closed pipe: quarter-wave modes (2n+1) pi c / (2 L_e), L - 1 < L_e <= L, "
+                 "L_e = L - 1/2 at c = cs; flat and cylindrical q3 faces alike",
+    "face/damping D": "impedance reflection (c - beta) / (c + beta), beta = cs2 (1 - D) / (1 + D): "
+                      "mode decay per round trip on q1 and q3 walls",
+    "source/plate J'_z": "dipole plane waves at speed c, amplitude C / (cs2 + c) at c = cs, "
+                         "uniform across a pipe (sqrt g)",
+    "source/ring P": "radiated profile fits J0 / Y0 of the radial Bessel equation",
 }
 
 

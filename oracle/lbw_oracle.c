@@ -38,8 +38,12 @@
  *   R5 ghost values for the gradient at a non-periodic face: free -> rho copied; bounce-back
  *      (rigid) -> P mirrored (even); anti-bounce-back (Dirichlet) -> P mirrored with a sign
  *      change (odd); the ghost's metric is evaluated at the ghost position.  Walls are pinned
- *      by the annulus, closed-pipe and horn modes; the free (copy) face only by a uniform
- *      state staying uniform: it meets no closed form, parity unpinned for its reflection.
+ *      by the annulus, closed-pipe and horn modes.  The free (copy) face is pinned by the
+ *      open-closed pipe of Sec. IV.A: a channel closed by a wall and ended by a free face has
+ *      the quarter-wave modes (2n+1) pi c / (2 L_e), L - 1 < L_e <= L (L - 1/2 at c = cs),
+ *      in flat space and on a cylinder's q3 face.  The damping D of the bounce-back rule is
+ *      pinned by the impedance reflection coefficient (c - beta) / (c + beta),
+ *      beta = cs^2 (1 - D) / (1 + D), that the rule implies for the wave equation.
  *   R6 the metric is written in lattice coordinates q: x^a = x0^a + (q^a + 1/2) h^a, so
  *      g_q^{ab} = g^{ab} / (h_a h_b), sqrt(g_q) = h1 h2 h3 sqrt(g), G_q^a = G^a / h_a.
  *   R7 initial state at rest: J'(0) = 0 (Eq. JShifted), so the stored post-collision
@@ -48,7 +52,9 @@
  *   R8 harmonic sources (the paper imposes P, or J'_z for the plate, at source nodes): after
  *      each step the source nodes' populations become the equilibrium carrying the imposed
  *      value (apply_sources).  Pinned by the radiated cylindrical wave of a ring source
- *      matching the radial Bessel equation's solutions.
+ *      matching the radial Bessel equation's solutions, and by the plate's plane waves: a
+ *      dipole (opposite signs either side, speed c), amplitude C / (cs^2 + c) at c = cs from
+ *      the equilibrium of a running wave, uniform across a pipe (the sqrt(g) factor).
  *   Also corrected from the printed formulas (verified symbolically): trumpet
  *   Gamma^theta_{z theta} = lambda / Zc (printed lambda / Zc^2) and torus
  *   Gamma^r_{theta theta} = -(R + r cos phi) cos phi (printed with +); the contracted

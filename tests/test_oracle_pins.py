@@ -296,6 +296,159 @@ def test_free_faces_keep_a_uniform_state():
     assert np.abs(d.get_f() - f0).max() > 1e-3
 
 
+# ---------------------------------------------------------------- face rules ---------------
+#
+# The free face (Sec. IV.A: the ghost copies the node next to the face), the damping factor D
+# of the bounce-back wall (Sec. IV.A: f_out = D f_in) and the plate source (Sec. IV.A: the left
+# end moves as a rigid plate, J'_z = C sin(omega t)), each against what the paper and the wave
+# equation fix.  One-dimensional channels along an axis: n = 1 on the other two (periodic).
+
+def _channel(c, L, lo, hi, axis=2, damping=1.0, cs2=0.25):
+    n = [1, 1, 1]
+    n[axis] = L
+    bc = [BC_PERIODIC] * 6
+    bc[2 * axis], bc[2 * axis + 1] = lo, hi
+    return GridSpec(kind=KIND_CARTESIAN, n=tuple(n), h=(1, 1, 1), x0=(0, 0, 0), c=c, cs2=cs2,
+                    damping=damping, bc=tuple(bc))
+
+
+def _mode_angles(spec):
+    """Distinct non-zero eigen-angles (rad / step) of the step operator, ascending."""
+    a = np.abs(np.angle(np.linalg.eigvals(_step_matrix(spec))))
+    return np.unique(np.round(a[a > 1e-8], 10))
+
+
+@pytest.mark.parametrize("c", [0.5, 0.4, 0.3])
+def test_free_face_is_an_open_end(c):
+    """Sec. IV.A calls the pipe with a bounce-back wall at z = 0 and a free face at z = L an
+    open-closed pipe with modes omega_n = (2n+1) pi c / (2 L): the free face must release
+    pressure (odd multiples of a quarter wave), not reflect like a wall (multiples of a half
+    wave, n pi c / L, which the same channel with two walls shows).  Its effective length L_e
+    lies within the last cell; the quarter-wave family holds to lattice dispersion."""
+    L = 48
+    w = _mode_angles(_channel(c, L, BC_BOUNCE, BC_FREE))
+    L_e = math.pi * c / (2 * w[0])
+    assert L - 1 < L_e <= L, L_e
+    np.testing.assert_allclose(w[1:3] / w[0], [3.0, 5.0], rtol=2e-2)
+    closed = _mode_angles(_channel(c, L, BC_BOUNCE, BC_BOUNCE))
+    np.testing.assert_allclose(closed[:2], [math.pi * c / L, 2 * math.pi * c / L], rtol=5e-3)
+    assert abs(closed[0] - w[0]) > 0.3 * w[0]  # the free face is not a wall
+
+
+def test_free_face_at_cs_is_an_open_end_at_the_last_node():
+    """At c = cs the divergence term vanishes in flat space and the free face releases
+    pressure exactly at the last node's centre, half a cell inside the face: the open-closed
+    modes are (2n+1) pi c / (2 (L - 1/2)) to lattice dispersion (k^2 terms: 3e-5 on the
+    fundamental, 5e-4 on the third mode here).  A face half a cell further out (the wall
+    position) would be 1.6% off."""
+    c, L = 0.5, 64
+    w = _mode_angles(_channel(c, L, BC_BOUNCE, BC_FREE))
+    expect = [(2 * n + 1) * math.pi * c / (2 * (L - 0.5)) for n in range(3)]
+    assert w[0] == pytest.approx(expect[0], rel=1e-4)
+    np.testing.assert_allclose(w[1:3], expect[1:3], rtol=1e-3)
+
+
+def test_free_face_in_curved_coordinates_reflects_like_flat_space():
+    """The q3 face of a cylinder (g^33 = 1, sqrt g independent of z): the axial modes of a
+    rigid annular pipe, closed at z = 0 and free at z = L, are the flat channel's eigen-angles
+    to rounding (the radially uniform axial modes are exact eigenvectors of both operators)."""
+    c, L = 0.4, 16
+    flat = _mode_angles(_channel(c, L, BC_BOUNCE, BC_FREE))
+    cyl = GridSpec(kind=KIND_CYLINDRICAL, n=(3, 4, L), h=(1, 2 * math.pi / 4, 1), x0=(3, 0, 0),
+                   c=c, bc=(BC_BOUNCE, BC_BOUNCE, 0, 0, BC_BOUNCE, BC_FREE))
+    a = np.abs(np.angle(np.linalg.eigvals(_step_matrix(cyl))))
+    for w in flat[:4]:
+        assert np.min(np.abs(a - w)) < 1e-9, w
+
+
+def _impedance_reflection(c, D, cs2=0.25):
+    """Reflection coefficient of the damped bounce-back wall for the wave equation.  Near the
+    wall the populations are their equilibria to first order, f_i ~ w_i (rho + xi_i j / cs2);
+    the wall rule f_out = D f_in (Sec. IV.A) then gives rho - j / cs2 = D (rho + j / cs2),
+    i.e. the impedance condition J = beta P with beta = cs2 (1 - D) / (1 + D).  A plane wave
+    P = A e^{i(kz - wt)} + B e^{-i(kz + wt)} with J = c (A e^{...} - B e^{...}) meets it with
+    B / A = (c - beta) / (c + beta)."""
+    beta = cs2 * (1 - D) / (1 + D)
+    return (c - beta) / (c + beta)
+
+
+@pytest.mark.parametrize("axis", [0, 2], ids=["q1", "q3"])
+@pytest.mark.parametrize("c,D", [(0.5, 0.9), (0.4, 0.9), (0.4, 0.65)])
+def test_damped_wall_reflects_with_the_impedance_coefficient(c, D, axis):
+    """A channel with a damped bounce-back wall at one end and a lossless anti-bounce-back
+    wall at the other: every standing wave loses the factor r of the damped wall once per
+    round trip of 2 L / c steps, so its eigenvalue has |lambda| = r^(c / 2L) per step.  A
+    factor D placed on the wrong populations, on both walls, or squared fails this."""
+    L = 32
+    spec = _channel(c, L, BC_BOUNCE, BC_ANTIBOUNCE, axis=axis, damping=D)
+    ev = np.linalg.eigvals(_step_matrix(spec))
+    ang = np.abs(np.angle(ev))
+    keep = ang > 1e-8
+    order = np.argsort(ang[keep])
+    decay = -np.log(np.abs(ev[keep][order]))  # per step, pairs of conjugates
+    expect = -math.log(_impedance_reflection(c, D)) * c / (2 * L)
+    assert decay[0] == pytest.approx(expect, rel=5e-3)
+    assert decay[2] == pytest.approx(expect, rel=3e-2)  # the second mode, dispersion larger
+    lossless = np.linalg.eigvals(_step_matrix(spec.with_(damping=1.0)))
+    assert np.abs(lossless).max() == pytest.approx(1.0, abs=1e-9)
+
+
+def _fit_sine(y, t, om):
+    M = np.stack([np.sin(om * t), np.cos(om * t)], 1)
+    (a, b), *_ = np.linalg.lstsq(M, y, rcond=None)
+    return math.hypot(a, b), math.atan2(b, a)
+
+
+@pytest.mark.parametrize("om", [0.05, 0.1])
+def test_plate_source_radiates_a_dipole_plane_wave(om):
+    """The plate source (kind 1) imposes J'_z = C sin(omega t) at its node and keeps the
+    node's density.  In a long channel it radiates plane waves of the drive frequency at
+    speed c in both directions, with opposite sign (a velocity source: J = +cP to the right,
+    J = -cP to the left) and P = 0 at the plate.  At c = cs the outgoing population of the
+    source, w_1 J / cs^2 = C / 2, equals that of a right-running wave of the equilibrium,
+    w_1 (P + c P / cs^2), so P = C / (cs^2 + c); a missing or doubled J' fails the amplitude,
+    a flipped sign the phase."""
+    c, L, s, d, C = 0.5, 800, 400, 80, 0.7
+    spec = _channel(c, L, BC_ANTIBOUNCE, BC_ANTIBOUNCE)
+    g = oracle.OracleGrid(spec)
+    g.init(np.zeros((0, 5)))
+    g.set_sources([[0, 0, s]], kind=1, amp=C, omega=om)
+    g.set_probes([[0, 0, s + d], [0, 0, s - d], [0, 0, s], [0, 0, s + d + 25]], 900)
+    g.step(900)
+    x = g.read_probes()
+    t = np.arange(1, 901)
+    sel = t > d / c + 150  # after the front and its transient have passed, before any echo
+    (ar, pr), (al, pl), (a0, _), (a2, p2) = [_fit_sine(x[k, sel], t[sel], om) for k in range(4)]
+    assert ar == pytest.approx(C / (0.25 + c), rel=2e-3)
+    assert al == pytest.approx(ar, rel=1e-12) and a0 < 1e-12
+    assert abs(math.remainder(pl - pr - math.pi, 2 * math.pi)) < 1e-9  # opposite sign
+    # phase speed c between the two right-hand probes (lattice dispersion < 1%)
+    assert abs(math.remainder(pr - p2 - om * 25 / c, 2 * math.pi)) < 1e-2 * om * 25 / c
+    # the right-running wave has the sign of J: P(s + d, t) ~ +A sin(omega (t - d / c))
+    assert abs(math.remainder(pr + om * d / c, 2 * math.pi)) < 0.35
+
+
+def test_plate_source_carries_sqrt_g():
+    """In a rigid annular pipe the plate source sets sqrt(g) J'_z = sqrt(g) C sin(omega t) over
+    the cross-section, so the radiated axial wave is uniform in r and as strong as in the flat
+    channel (the same populations per unit sqrt g).  Dropping sqrt g would make J fall like
+    1 / r across the pipe."""
+    c, om, C, L, s = 0.5, 0.08, 1.0, 400, 200
+    n1, n2 = 4, 4
+    cyl = GridSpec(kind=KIND_CYLINDRICAL, n=(n1, n2, L), h=(1, 2 * math.pi / n2, 1),
+                   x0=(4, 0, 0), c=c, bc=(BC_BOUNCE, BC_BOUNCE, 0, 0, BC_ANTIBOUNCE, BC_ANTIBOUNCE))
+    g = oracle.OracleGrid(cyl)
+    g.init(np.zeros((0, 5)))
+    g.set_sources([[i, j, s] for i in range(n1) for j in range(n2)], kind=1, amp=C, omega=om)
+    g.set_probes([[i, 1, s + 60] for i in range(n1)], 600)
+    g.step(600)
+    x = g.read_probes()
+    t = np.arange(1, 601)
+    sel = t > 60 / c + 150
+    amps = [_fit_sine(x[k, sel], t[sel], om)[0] for k in range(n1)]
+    np.testing.assert_allclose(amps, C / (0.25 + c), rtol=3e-3)
+
+
 # ---------------------------------------------------------------- Bessel modes ------------
 
 def _annulus_spec(Nr=32, Nt=128, r_in=8.0, c=0.4, Nz=1, L=None):
