@@ -139,7 +139,8 @@ lbw_status lbw_probe_read(lbw_grid* g, double* host_out, int64_t cap_per_probe,
  * smallest power of two >= 4 T, |DFT|^2, the k strongest local maxima above 1e-3 of the
  * largest (sorted by frequency), each refined by a parabola through log-power and 40
  * golden-section steps on the windowed DTFT over +-1 bin.  host_freq / host_amp receive up
- * to k values (rad/step, amplitude 2 |X| / sum w); *n_found how many. */
+ * to k values (rad/step, amplitude 2 |X| / sum w); *n_found how many.  LBW_EUNSTABLE (and no
+ * peaks) when the series holds a non-finite value; the same holds for every spectrum call. */
 lbw_status lbw_spectrum(lbw_grid* g, int32_t probe, int32_t k, double* host_freq,
                         double* host_amp, int32_t* n_found);
 
@@ -165,16 +166,19 @@ lbw_status lbw_spectrum_series(const double* host_x, int64_t T, int32_t n_series
  *  - All workspace lives in one fixed device array of about 2.6 MB inside the library, which
  *    every GPU that loads the library holds until the process exits.  No call here allocates
  *    or frees device memory.
- *  - The first call on a device (with that device current) looks up the array's device
- *    address; make that first call before any stream capture.
+ *  - The array's device address is looked up (cudaGetSymbolAddress) by the first call in each
+ *    device context, with that device current, and cached under the context's ID; a context
+ *    created after a device reset gets a fresh look-up.
  *  - Every call on a device shares the array and leaves its contents behind; calls whose work
- *    overlaps on the GPU (different streams, no ordering between them) race.  The call
- *    synchronises `stream` before returning. */
+ *    overlaps on the GPU (different streams, no ordering between them) race, so callers must
+ *    serialise them.  The call synchronises `stream` and copies its results to host memory
+ *    before returning, so it cannot be made while `stream` is being captured into a graph. */
 lbw_status lbw_spectrum_series_static(const double* dev_x, int64_t T, int32_t k, void* stream,
                                       double* host_freq, double* host_amp, int32_t* host_n_found);
 
 /* P = rho / sqrt(g) of the current state (rho = sum of the stored post-collision
- * populations; the relaxation conserves it), N doubles in the layout above. */
+ * populations; the relaxation conserves it), N doubles in the layout above.  The field is
+ * copied in every case; LBW_EUNSTABLE if any of its values is not finite. */
 lbw_status lbw_get_field(lbw_grid* g, double* host_P);
 
 /* Checkpoint / resume: the seven population planes as doubles (7 x N, same layout). */

@@ -566,7 +566,11 @@ lbw_status lbw_get_field(lbw_grid* g, double* host_P) {
   cudaFreeAsync(d, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_fail(e, "get_field");
-  return read_counters(g, nullptr);
+  const lbw_status st = read_counters(g, nullptr);
+  if (st != LBW_OK) return st;
+  for (int64_t x = 0; x < g->nn; ++x)
+    if (!std::isfinite(host_P[x])) return fail(LBW_EUNSTABLE, "field holds a non-finite value (unstable run)");
+  return LBW_OK;
 }
 
 lbw_status lbw_get_populations(lbw_grid* g, double* host_f) {

@@ -11,9 +11,11 @@
 //   4. each peak is refined by a parabola through log-power at j-1, j, j+1 and 40
 //      golden-section steps on the windowed DTFT over +-1 bin (one CTA per peak; the DTFT
 //      sum uses per-thread chunks with a rotation recurrence for e^{-i omega t}).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -249,65 +251,110 @@ __global__ void refine_kernel(const double* __restrict__ xw, long long T, const 
   }
 }
 
+// Workspace of one estimate, carved from one block of device memory sized for series of up to
+// T samples and transforms of up to M points: stats(4) | a(M) | b(M) | xw(T) | P(M/2+1) |
+// cand(M/4+1) | count | chosen(64) | n_chosen | freq(64) | amp(64).
+struct Workspace {
+  double* stats;
+  double2 *A, *B;
+  double* xw;
+  double* P;
+  long long* cand;
+  unsigned long long* count;
+  long long* chosen;
+  int* n_chosen;
+  double *freq, *amp;
+};
+
+constexpr size_t round16(size_t n) { return (n + 15) / 16 * 16; }
+
+constexpr size_t workspace_bytes(size_t M, size_t T) {
+  return round16(4 * 8) + 2 * round16(M * 16) + round16(T * 8) + round16((M / 2 + 1) * 8) +
+         round16((M / 4 + 1) * 8) + round16(8) + round16(64 * 8) + round16(8) + round16(64 * 8) +
+         round16(64 * 8);
+}
+
+Workspace carve(unsigned char* base, size_t M, size_t T) {
+  unsigned char* p = base;
+  auto take = [&](size_t n) { unsigned char* q = p; p += round16(n); return q; };
+  Workspace w;
+  w.stats = (double*)take(4 * 8);
+  w.A = (double2*)take(M * 16);
+  w.B = (double2*)take(M * 16);
+  w.xw = (double*)take(T * 8);
+  w.P = (double*)take((M / 2 + 1) * 8);
+  w.cand = (long long*)take((M / 4 + 1) * 8);
+  w.count = (unsigned long long*)take(8);
+  w.chosen = (long long*)take(64 * 8);
+  w.n_chosen = (int*)take(8);
+  w.freq = (double*)take(64 * 8);
+  w.amp = (double*)take(64 * 8);
+  return w;
+}
+
+// The estimator's launches on stream s and the copy of its results to the host (synchronous).
+// Every workspace value is written before it is read except the candidate counter, which is
+// cleared here, so a workspace may hold anything from an earlier call.  *finite is false when
+// the series' mean is not finite (a NaN or infinity in the series: an unstable run).
+cudaError_t run_estimator(const Workspace& w, const double* d_x, int64_t T, int nser,
+                          int32_t stride_series, int32_t k, bool lowest, double rel_power,
+                          cudaStream_t s, double* h_freq, double* h_amp, int32_t* h_n,
+                          bool* finite) {
+  long long M = 1;
+  while (M < 4 * T) M <<= 1;
+  // a launch error left behind by an unrelated earlier runtime call on this thread would
+  // otherwise be read back below as this call's failure
+  (void)cudaGetLastError();
+  cudaError_t e = cudaMemsetAsync(w.count, 0, 8, s);
+  const int blocks = 152 * 4;
+  if (e == cudaSuccess) {
+    stats_kernel<<<1, 1024, 0, s>>>(d_x, T, nser, stride_series, w.stats);
+    window_kernel<<<blocks, 256, 0, s>>>(d_x, T, nser, stride_series, w.stats, M, w.A, w.xw);
+    double2 *in = w.A, *out = w.B;
+    for (long long ns = 1; ns < M; ns <<= 1) {
+      stockham_kernel<<<blocks, 256, 0, s>>>(in, out, M, ns);
+      std::swap(in, out);
+    }
+    power_kernel<<<blocks, 256, 0, s>>>(in, M, w.P);
+    max_kernel<<<1, 1024, 0, s>>>(w.P, M, w.stats);
+    candidates_kernel<<<blocks, 256, 0, s>>>(w.P, M, w.stats, rel_power, w.cand, w.count);
+    select_kernel<<<1, 1024, 0, s>>>(w.P, w.cand, w.count, k, w.chosen, w.n_chosen, lowest);
+    refine_kernel<<<k, kThreads, 0, s>>>(w.xw, T, w.P, M, w.chosen, w.n_chosen, w.stats, w.freq, w.amp);
+    e = cudaGetLastError();
+  }
+  int nfound = 0;
+  double mean = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nfound, w.n_chosen, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&mean, w.stats, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  *finite = std::isfinite(mean);
+  if (!*finite) nfound = 0;
+  if (e == cudaSuccess && nfound > 0) {
+    e = cudaMemcpyAsync(h_freq, w.freq, sizeof(double) * nfound, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_amp, w.amp, sizeof(double) * nfound, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e == cudaSuccess) *h_n = nfound;
+  return e;
+}
+
 }  // namespace
 
 lbw_status spectrum_device(const double* d_x, int64_t T, int32_t n_series, int32_t stride_series,
                            bool sum_all, int32_t k, cudaStream_t s, double* h_freq,
                            double* h_amp, int32_t* h_n, bool lowest, double rel_power) {
-  const int nser = sum_all ? n_series : 1;
   long long M = 1;
   while (M < 4 * T) M <<= 1;
-  // one scratch allocation: stats(4) | a(M) | b(M) | xw(T) | P(M/2+1) | cand(M/4+1) |
-  //                          count | chosen(64) | n_chosen | freq(64) | amp(64)
-  const size_t bytes = 4 * 8 + 2 * (size_t)M * 16 + (size_t)T * 8 + ((size_t)M / 2 + 1) * 8 +
-                       ((size_t)M / 4 + 1) * 8 + 8 + 64 * 8 + 8 + 64 * 8 + 64 * 8;
   unsigned char* base = nullptr;
-  LBW_CUDA(cudaMallocAsync((void**)&base, bytes, s));
-  unsigned char* p = base;
-  auto take = [&](size_t n) { unsigned char* q = p; p += (n + 15) / 16 * 16; return q; };
-  double* stats = (double*)take(4 * 8);
-  double2* A = (double2*)take((size_t)M * 16);
-  double2* B = (double2*)take((size_t)M * 16);
-  double* xw = (double*)take((size_t)T * 8);
-  double* P = (double*)take(((size_t)M / 2 + 1) * 8);
-  long long* cand = (long long*)take(((size_t)M / 4 + 1) * 8);
-  unsigned long long* count = (unsigned long long*)take(8);
-  long long* chosen = (long long*)take(64 * 8);
-  int* n_chosen = (int*)take(8);
-  double* freq = (double*)take(64 * 8);
-  double* amp = (double*)take(64 * 8);
-  (void)p;
-
-  // a launch error left behind by an unrelated earlier runtime call on this thread would
-  // otherwise be read back below as this call's failure
-  (void)cudaGetLastError();
-  cudaError_t e = cudaMemsetAsync(count, 0, 8, s);
-  const int blocks = 152 * 4;
-  if (e == cudaSuccess) {
-    stats_kernel<<<1, 1024, 0, s>>>(d_x, T, nser, stride_series, stats);
-    window_kernel<<<blocks, 256, 0, s>>>(d_x, T, nser, stride_series, stats, M, A, xw);
-    double2 *in = A, *out = B;
-    for (long long ns = 1; ns < M; ns <<= 1) {
-      stockham_kernel<<<blocks, 256, 0, s>>>(in, out, M, ns);
-      std::swap(in, out);
-    }
-    power_kernel<<<blocks, 256, 0, s>>>(in, M, P);
-    max_kernel<<<1, 1024, 0, s>>>(P, M, stats);
-    candidates_kernel<<<blocks, 256, 0, s>>>(P, M, stats, rel_power, cand, count);
-    select_kernel<<<1, 1024, 0, s>>>(P, cand, count, k, chosen, n_chosen, lowest);
-    refine_kernel<<<k, kThreads, 0, s>>>(xw, T, P, M, chosen, n_chosen, stats, freq, amp);
-    e = cudaGetLastError();
-  }
-  int nfound = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&nfound, n_chosen, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess && nfound > 0) {
-    e = cudaMemcpyAsync(h_freq, freq, sizeof(double) * nfound, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_amp, amp, sizeof(double) * nfound, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  }
+  LBW_CUDA(cudaMallocAsync((void**)&base, workspace_bytes((size_t)M, (size_t)T), s));
+  const Workspace w = carve(base, (size_t)M, (size_t)T);
+  int32_t nfound = 0;
+  bool finite = true;
+  const cudaError_t e = run_estimator(w, d_x, T, sum_all ? n_series : 1, stride_series, k, lowest,
+                                      rel_power, s, h_freq, h_amp, &nfound, &finite);
   cudaFreeAsync(base, s);
   if (e != cudaSuccess) return cuda_fail(e, "spectrum");
+  if (!finite) return fail(LBW_EUNSTABLE, "spectrum: the series holds a non-finite value (unstable run)");
   *h_n = nfound;
   return LBW_OK;
 }
@@ -323,27 +370,72 @@ lbw_status spectrum_device(const double* d_x, int64_t T, int32_t n_series, int32
 
 namespace lbw {
 namespace {
-
 constexpr int64_t kStaticMaxT = 16384;
-
-constexpr size_t round16(size_t n) { return (n + 15) / 16 * 16; }
-constexpr size_t static_scratch_bytes() {
-  // same layout as spectrum_device for T = kStaticMaxT (M = 4 T rounded up to a power of two)
-  return round16(4 * 8) + 2 * round16((size_t)4 * kStaticMaxT * 16) + round16(kStaticMaxT * 8) +
-         round16(((size_t)4 * kStaticMaxT / 2 + 1) * 8) + round16(((size_t)4 * kStaticMaxT / 4 + 1) * 8) +
-         round16(8) + round16(64 * 8) + round16(8) + round16(64 * 8) + round16(64 * 8);
-}
-
+constexpr size_t kStaticMaxM = 4 * (size_t)kStaticMaxT;  // a power of two: M of the largest T
 }  // namespace
 }  // namespace lbw
 
 // The workspace.  In host code this name is only a host-side handle: its device address comes
-// from cudaGetSymbolAddress, once per device.
-static __device__ __align__(256) unsigned char g_spectrum_scratch[lbw::static_scratch_bytes()];
+// from cudaGetSymbolAddress, looked up once per device context (static_workspace below).
+static __device__ __align__(256) unsigned char
+    g_spectrum_scratch[lbw::workspace_bytes(lbw::kStaticMaxM, lbw::kStaticMaxT)];
 
 namespace {
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique ID of the calling thread's current context (0 when there is none or the driver does
+// not say).  IDs are never reused within a process, so a context created after a device reset
+// never matches an ID cached before it.
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(fn);
+    (void)cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+struct StaticAddr {
+  unsigned long long ctx_id = 0;
+  void* ptr = nullptr;
+};
 std::mutex g_static_mu;
-void* g_static_addr[256] = {nullptr};
+StaticAddr g_static_addr[256];
+
+// Device address of the workspace on the current device.  Set-up, with that device current:
+// cudaGetSymbolAddress, once per device context; the address is cached under the context's ID
+// and looked up again when the device's context has changed (after cudaDeviceReset).
+cudaError_t static_workspace(int dev, unsigned char** out) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  StaticAddr& a = g_static_addr[dev];
+  const unsigned long long id = current_context_id();
+  if (id == 0 || a.ptr == nullptr || a.ctx_id != id) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_spectrum_scratch);
+    if (e != cudaSuccess) return e;
+    a.ptr = ptr;
+    a.ctx_id = current_context_id();  // the look-up makes the device's primary context current
+  }
+  *out = static_cast<unsigned char*>(a.ptr);
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" lbw_status lbw_spectrum_series_static(const double* dev_x, int64_t T, int32_t k,
@@ -359,61 +451,15 @@ extern "C" lbw_status lbw_spectrum_series_static(const double* dev_x, int64_t T,
   LBW_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) return fail(LBW_EINVAL, "device ordinal out of range");
   unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {  // first call on this device: resolve the array's device address
-      void* ptr = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&ptr, g_spectrum_scratch);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_spectrum_scratch)");
-      g_static_addr[dev] = ptr;
-    }
-    base = static_cast<unsigned char*>(g_static_addr[dev]);
-  }
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  long long M = 1;
-  while (M < 4 * T) M <<= 1;
-  unsigned char* p = base;
-  auto take = [&](size_t n) { unsigned char* q = p; p += round16(n); return q; };
-  double* stats = (double*)take(4 * 8);
-  double2* A = (double2*)take((size_t)4 * kStaticMaxT * 16);
-  double2* B = (double2*)take((size_t)4 * kStaticMaxT * 16);
-  double* xw = (double*)take((size_t)kStaticMaxT * 8);
-  double* P = (double*)take(((size_t)4 * kStaticMaxT / 2 + 1) * 8);
-  long long* cand = (long long*)take(((size_t)4 * kStaticMaxT / 4 + 1) * 8);
-  unsigned long long* count = (unsigned long long*)take(8);
-  long long* chosen = (long long*)take(64 * 8);
-  int* n_chosen = (int*)take(8);
-  double* freq = (double*)take(64 * 8);
-  double* amp = (double*)take(64 * 8);
-
-  // the candidate counter is the only value read before it is written; the array keeps the
-  // previous call's contents
-  cudaError_t e = cudaMemsetAsync(count, 0, 8, s);
-  const int blocks = 152 * 4;
-  if (e == cudaSuccess) {
-    stats_kernel<<<1, 1024, 0, s>>>(dev_x, T, 1, T, stats);
-    window_kernel<<<blocks, 256, 0, s>>>(dev_x, T, 1, T, stats, M, A, xw);
-    double2 *in = A, *out = B;
-    for (long long ns = 1; ns < M; ns <<= 1) {
-      stockham_kernel<<<blocks, 256, 0, s>>>(in, out, M, ns);
-      std::swap(in, out);
-    }
-    power_kernel<<<blocks, 256, 0, s>>>(in, M, P);
-    max_kernel<<<1, 1024, 0, s>>>(P, M, stats);
-    candidates_kernel<<<blocks, 256, 0, s>>>(P, M, stats, 1e-3, cand, count);
-    select_kernel<<<1, 1024, 0, s>>>(P, cand, count, k, chosen, n_chosen, false);
-    refine_kernel<<<k, kThreads, 0, s>>>(xw, T, P, M, chosen, n_chosen, stats, freq, amp);
-    e = cudaGetLastError();
-  }
-  int nfound = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&nfound, n_chosen, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess && nfound > 0) {
-    e = cudaMemcpyAsync(host_freq, freq, sizeof(double) * nfound, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_amp, amp, sizeof(double) * nfound, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  }
+  cudaError_t e = static_workspace(dev, &base);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_spectrum_scratch)");
+  const Workspace w = carve(base, kStaticMaxM, (size_t)kStaticMaxT);
+  int32_t nfound = 0;
+  bool finite = true;
+  e = run_estimator(w, dev_x, T, 1, (int32_t)T, k, false, 1e-3,
+                    reinterpret_cast<cudaStream_t>(stream), host_freq, host_amp, &nfound, &finite);
   if (e != cudaSuccess) return cuda_fail(e, "lbw_spectrum_series_static");
+  if (!finite) return fail(LBW_EUNSTABLE, "spectrum: the series holds a non-finite value");
   *host_n_found = nfound;
   return LBW_OK;
 }
