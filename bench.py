@@ -1,17 +1,20 @@
 """Benchmark of the fused curvilinear wave-LBM sweep on GB300.
 
-One benchmark step = one full run of the hot path on the 3-D cylinder workload
-(128 x 128 x 256 nodes, FP32 storage, 20 000 time steps of the fused stream + collide
-kernel with 16 probes recorded every step, then the device spectrum of the summed probes).
-Metric: MLUPS = nodes x time steps / seconds / 1e6 (whole job, all ranks).
+One benchmark step = one run of the whole hot path on the torus workload (r 192 x theta 1024
+x phi 256 = 50,331,648 nodes, R / a = 3, FP32 storage, one seeded Gaussian pulse): 2000 time
+steps of the fused stream + collide kernel with 64 probes recorded every step, then the device
+spectrum of the summed probes.  Metric: MLUPS = nodes x time steps / seconds / 1e6 (whole
+job, all ranks).
 
   value  device-timed: the initial state is rebuilt (untimed) before every step, then
          CUDA events on the library's stream bracket lbw_step + lbw_spectrum.
   e2e    the same run through the public C ABI from host buffers: lbw_init (host pulses),
          lbw_probe (host probe nodes), lbw_step, lbw_probe_read (series to host) and
          lbw_spectrum, all inside the timed region.
-The working set (two population buffers, 470 MB) is larger than the 129 MB L2, so no flush
-is needed between steps.  --impl reference times the FP64 CPU oracle on the same workload.
+The torus's working set (two population buffers, 2.82 GB in FP32) is 22 times the 129 MB L2,
+so no flush is needed between steps.  --workload selects the other lattices (their own time
+step counts unless --lbm-steps is given); --impl reference times the FP64 CPU oracle on the
+same workload.
 """
 from __future__ import annotations
 
@@ -31,7 +34,9 @@ sys.path.insert(0, ROOT)
 
 import lbw_workloads as W  # noqa: E402
 
-LBM_STEPS = 20000
+# time steps per benchmark step: the torus runs a stated 2000 (its full 50 000-step run takes
+# 24 s per step on the GPU); the other workloads run their own full length
+BENCH_TIME_STEPS = {"torus": 2000}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -119,12 +124,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-WORKLOAD = "cylinder"
+WORKLOAD = "torus"
 PREC_OVERRIDE = None
 
 
 def workload():
-    """The benchmark workload (cylinder by default; --workload / --prec select another)."""
+    """The benchmark workload (torus by default; --workload / --prec select another)."""
     wl = W.workload(WORKLOAD)
     if PREC_OVERRIDE is not None:
         wl.spec = wl.spec.with_(prec=PREC_OVERRIDE)
@@ -169,7 +174,7 @@ def run_ensemble(args):
     prec = PREC_OVERRIDE if PREC_OVERRIDE is not None else W.PREC_F32
     specs, _ = W.ensemble(args.members, seed=5, prec=prec)
     nodes = sum(s.nodes for s in specs)
-    lbm_steps = args.lbm_steps if args.lbm_steps != LBM_STEPS else ENSEMBLE_STEPS
+    lbm_steps = args.lbm_steps if args.lbm_steps is not None else ENSEMBLE_STEPS
     stream = torch.cuda.Stream()
     sh = lbw.ctypes.c_void_p(stream.cuda_stream)
     b = lbw.Batch(specs, stream=sh)
@@ -339,7 +344,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     g.step(1)
     t1 = time.perf_counter() - t0
-    per_step = max(1, int(20.0 / max(t1, 1e-6)))  # ~20 s of host work per benchmark step
+    per_step = max(1, int(8.0 / max(t1, 1e-6)))  # ~8 s of host work per benchmark step
     for _ in range(args.warmup):
         g.step(1)
     times = []
@@ -372,10 +377,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--lbm-steps", type=int, default=LBM_STEPS,
-                    help="time steps per benchmark step (default: the workload's 20000)")
+    ap.add_argument("--lbm-steps", type=int, default=None,
+                    help="time steps per benchmark step (default: 2000 for the torus, the "
+                         "workload's full length otherwise, 512 for the ensemble)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cylinder",
+    ap.add_argument("--workload", default="torus",
                     choices=["cylinder", "disk", "trumpet", "torus", "ensemble"])
     ap.add_argument("--members", type=int, default=512,
                     help="ensemble members (--workload ensemble)")
@@ -412,7 +418,7 @@ def main():
 
     wl = workload()
     spec = wl.spec
-    lbm_steps = args.lbm_steps if args.lbm_steps != LBM_STEPS else wl.steps
+    lbm_steps = args.lbm_steps if args.lbm_steps is not None else BENCH_TIME_STEPS.get(WORKLOAD, wl.steps)
     stream = torch.cuda.Stream()
     sh = lbw.ctypes.c_void_p(stream.cuda_stream)
     grid = lbw.Grid(spec, stream=sh)
@@ -463,7 +469,7 @@ def main():
     kernel_ms = sum(step_ms) / (args.steps * lbm_steps)
     achieved = spec.nodes * bytes_per_node / (kernel_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = profiled_traffic() if (WORKLOAD == "cylinder" and PREC_OVERRIDE is None) else None
+    traffic = profiled_traffic(WORKLOAD, spec)
 
     # ---- end to end through the C ABI with host buffers
     host_pulses = np.ascontiguousarray(wl.pulses)
@@ -515,13 +521,11 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": {W.PREC_F64: "f64", W.PREC_F32: "f32", W.PREC_F16S: "f16 storage / f32 math",
                   W.PREC_BF16S: "bf16 storage / f32 math"}[spec.prec], "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD} {spec.n[0]}x{spec.n[1]}x{spec.n[2]}, "
-                               f"{lbm_steps} time steps + spectrum per step, "
-                               f"{nprobe} probes, 8 random-phase Gaussian pulses",
+        "config": {"workload": f"{wl.notes}, {spec.nodes:,} nodes, {lbm_steps} time steps + "
+                               f"spectrum per step, {nprobe} probes, {pulse_label(wl)}",
                    "nodes": spec.nodes, "time_steps_per_step": lbm_steps, "c": spec.c,
                    "r_in": spec.x0[0],
-                   "l2": f"working set {2 * 7 * spec.nodes * elem / 1e6:.0f} MB vs 129 MB L2 "
-                         "(no flush between steps)",
+                   "l2": l2_note(2 * 7 * spec.nodes * elem),
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -570,7 +574,10 @@ def f64_deviation(lbw, wl, lbm_steps, grid, stream_handle, k=8):
     return out
 
 
-PROFILE = os.path.join(ROOT, "profiles", "step_tma_kernel_cylinder_128x128x256_f32.md")
+PROFILES = {
+    ("torus", W.PREC_F32): os.path.join(ROOT, "profiles", "step_tma_kernel_torus_192x1024x256_f32.md"),
+    ("cylinder", W.PREC_F32): os.path.join(ROOT, "profiles", "step_tma_kernel_cylinder_128x128x256_f32.md"),
+}
 ENSEMBLE_PROFILE = os.path.join(ROOT, "profiles", "batch_tma_kernel_ensemble_32_trumpets_f32.md")
 
 
@@ -595,11 +602,31 @@ def _profile_fields(path):
     return fields
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None when
-    the kernel source changed since the counters were taken."""
+def pulse_label(wl):
+    """What the initial field is, from the workload's own pulse list."""
+    n = len(wl.pulses)
+    phased = bool(np.any(np.abs(wl.pulses[:, 4]) != 1.0))
+    kind = "random-phase " if phased else ""
+    return f"{n} {kind}Gaussian pulse{'s' if n != 1 else ''} (sigma {wl.pulses[0, 3]:g} cells)"
+
+
+def l2_note(working_set_bytes):
+    """Working set against the 129 MB L2: the benchmark does not flush L2 between steps, which
+    is valid only when the population buffers do not fit in it."""
+    ratio = working_set_bytes / 129e6
+    if ratio >= 4.0:
+        return (f"working set {working_set_bytes / 1e6:.0f} MB = {ratio:.1f}x the 129 MB L2 "
+                "(no flush between steps)")
+    return (f"working set {working_set_bytes / 1e6:.0f} MB = only {ratio:.1f}x the 129 MB L2: "
+            "part of it stays L2-resident between time steps")
+
+
+def profiled_traffic(workload_name, spec):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary of this workload
+    and storage, or None when there is none or the kernel source changed since the counters
+    were taken."""
     try:
-        fields = _profile_fields(PROFILE)
+        fields = _profile_fields(PROFILES[(workload_name, spec.prec)])
         if fields.get("step_source_sha256_16") != lbw_kernel_hash():
             return None
         return int(fields["traffic_bytes_per_launch"])

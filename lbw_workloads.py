@@ -195,19 +195,19 @@ def workload(name: str) -> Workload:
     if name == "disk":
         s = disk()
         return Workload("disk", s, 4000, pulses(s, 1, 1), probes(s, 1, 4),
-                        "2-D polar annulus 128x128, FP64")
+                        "2-D polar annulus r 128 x theta 128")
     if name == "cylinder":
         s = cylinder()
         return Workload("cylinder", s, 20000, pulses(s, 2, 8, random_phase=True),
-                        probes(s, 2, 16), "3-D cylinder 128x128x256, FP32")
+                        probes(s, 2, 16), "cylinder r 128 x theta 128 x z 256")
     if name == "trumpet":
         s = trumpet()
         return Workload("trumpet", s, 50000, pulses(s, 3, 1), probes(s, 3, 32),
-                        "exponential horn 256x256x512")
+                        "exponential-flare trumpet r 256 x theta 256 x z 512")
     if name == "torus":
         s = torus()
         return Workload("torus", s, 50000, pulses(s, 4, 1), probes(s, 4, 64),
-                        "torus 192x1024x256, R/a = 3")
+                        "torus r 192 x theta (major) 1024 x phi (minor) 256, R/a = 3")
     raise KeyError(name)
 
 
