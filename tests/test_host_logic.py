@@ -51,15 +51,19 @@ def test_profiled_traffic_follows_the_kernel_source(monkeypatch):
     """bench.py reports ncu DRAM traffic only while the kernel source still hashes to the
     value recorded with the counters; the ensemble's bytes per node scale with its nodes."""
     import bench
-    step = bench._profile_fields(bench.PROFILE)
+    import lbw_workloads as W
+    spec = W.workload("cylinder").spec
+    step = bench._profile_fields(bench.PROFILES[("cylinder", W.PREC_F32)])
     ens = bench._profile_fields(bench.ENSEMBLE_PROFILE)
     real = {"lbw_step.cu": step["step_source_sha256_16"],
             "lbw_batch.cu": ens["batch_source_sha256_16"]}
     monkeypatch.setattr(bench, "source_hash", lambda name: real[name])
-    assert bench.profiled_traffic() == int(step["traffic_bytes_per_launch"])
+    assert bench.profiled_traffic("cylinder", spec) == int(step["traffic_bytes_per_launch"])
+    assert bench.profiled_traffic("cylinder", spec.with_(prec=W.PREC_F16S)) is None
+    assert bench.profiled_traffic("disk", W.workload("disk").spec) is None
     per_node = float(ens["traffic_bytes_per_node"])
     assert bench.profiled_ensemble_traffic(1000) == round(per_node * 1000)
     monkeypatch.setattr(bench, "source_hash", lambda name: "0" * 16)
-    assert bench.profiled_traffic() is None
+    assert bench.profiled_traffic("cylinder", spec) is None
     assert bench.profiled_ensemble_traffic(1000) is None
 
