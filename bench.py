@@ -126,11 +126,12 @@ class ClockSampler:
 
 WORKLOAD = "torus"
 PREC_OVERRIDE = None
+SHAPE = None
 
 
 def workload():
     """The benchmark workload (torus by default; --workload / --prec select another)."""
-    wl = W.workload(WORKLOAD)
+    wl = W.workload(WORKLOAD, SHAPE)
     if PREC_OVERRIDE is not None:
         wl.spec = wl.spec.with_(prec=PREC_OVERRIDE)
     return wl
@@ -397,9 +398,13 @@ def main():
                          "GPU and report the field and mode-frequency deviations")
     ap.add_argument("--prec", default=None, choices=["f64", "f32", "f16s", "bf16s"],
                     help="storage override (default: the workload's own)")
+    ap.add_argument("--shape", default=None, metavar="N1,N2,N3",
+                    help="resize the workload's lattice (smaller profiling captures)")
     args = ap.parse_args()
-    global WORKLOAD, PREC_OVERRIDE
+    global WORKLOAD, PREC_OVERRIDE, SHAPE
     WORKLOAD = args.workload
+    if args.shape:
+        SHAPE = tuple(int(v) for v in args.shape.split(","))
     if args.prec:
         PREC_OVERRIDE = {"f64": W.PREC_F64, "f32": W.PREC_F32, "f16s": W.PREC_F16S,
                          "bf16s": W.PREC_BF16S}[args.prec]
@@ -469,7 +474,7 @@ def main():
     kernel_ms = sum(step_ms) / (args.steps * lbm_steps)
     achieved = spec.nodes * bytes_per_node / (kernel_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = profiled_traffic(WORKLOAD, spec)
+    traffic = profiled_traffic(WORKLOAD, spec) if SHAPE is None else None
 
     # ---- end to end through the C ABI with host buffers
     host_pulses = np.ascontiguousarray(wl.pulses)

@@ -188,6 +188,16 @@ lbw_status lbw_set_populations(lbw_grid* g, const double* host_f);
 /* Number of time steps advanced since lbw_init. */
 lbw_status lbw_step_count(lbw_grid* g, int64_t* out);
 
+/* Failure injection for tests of the timeout path; the paper has no counterpart.  From the
+ * next time step on, the step kernel's consumer warps wait on a barrier that no copy ever
+ * completes.  The bounded wait runs out after a few hundred tries (under a millisecond), the
+ * step raises its timeout flag, and every CTA leaves once the copies it issued have landed,
+ * exactly as after a lost copy, with no device fault and no hang.  Calls that synchronise
+ * then return LBW_ETIMEOUT; lbw_init clears the request and the flag.  LBW_ESTATE before
+ * lbw_init; LBW_EINVAL on lattices that run the register-pipelined kernel (q2 extent not a
+ * multiple of the tile width, or periodic q1), which has no device waits. */
+lbw_status lbw_inject_wait_timeout(lbw_grid* g);
+
 /* Frees the grid's device memory (stream-ordered) and graphs; NULL is allowed. */
 void lbw_destroy(lbw_grid* g);
 

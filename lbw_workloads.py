@@ -191,23 +191,30 @@ class Workload:
     extra: dict = field(default_factory=dict)
 
 
-def workload(name: str) -> Workload:
+def workload(name: str, shape=None) -> Workload:
+    """A benchmark workload; `shape` = (n1, n2, n3) resizes its lattice (same kind, wave speed,
+    faces and seeds; the inner radius and the torus's R follow the new sizes as they do for the
+    default), which serves smaller profiling captures of the same kernels."""
     if name == "disk":
-        s = disk()
+        n = shape or (128, 128, 1)
+        s = disk(n[0], n[1])
         return Workload("disk", s, 4000, pulses(s, 1, 1), probes(s, 1, 4),
-                        "2-D polar annulus r 128 x theta 128")
+                        f"2-D polar annulus r {n[0]} x theta {n[1]}")
     if name == "cylinder":
-        s = cylinder()
+        n = shape or (128, 128, 256)
+        s = cylinder(*n)
         return Workload("cylinder", s, 20000, pulses(s, 2, 8, random_phase=True),
-                        probes(s, 2, 16), "cylinder r 128 x theta 128 x z 256")
+                        probes(s, 2, 16), f"cylinder r {n[0]} x theta {n[1]} x z {n[2]}")
     if name == "trumpet":
-        s = trumpet()
+        n = shape or (256, 256, 512)
+        s = trumpet(*n)
         return Workload("trumpet", s, 50000, pulses(s, 3, 1), probes(s, 3, 32),
-                        "exponential-flare trumpet r 256 x theta 256 x z 512")
+                        f"exponential-flare trumpet r {n[0]} x theta {n[1]} x z {n[2]}")
     if name == "torus":
-        s = torus()
+        n = shape or (192, 1024, 256)
+        s = torus(*n)
         return Workload("torus", s, 50000, pulses(s, 4, 1), probes(s, 4, 64),
-                        "torus r 192 x theta (major) 1024 x phi (minor) 256, R/a = 3")
+                        f"torus r {n[0]} x theta (major) {n[1]} x phi (minor) {n[2]}, R/a = 3")
     raise KeyError(name)
 
 

@@ -322,7 +322,7 @@ lbw_status lbw_create_grid(const lbw_grid_desc* desc, void* stream, lbw_grid** o
   const size_t rs = real_size(d.prec);
   const size_t tbytes = tab.size() * rs;
   cudaError_t e = cudaMallocAsync(&g->table, tbytes, g->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&g->counters, 4 * sizeof(unsigned long long), g->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&g->counters, 5 * sizeof(unsigned long long), g->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBW_ENOMEM, "table allocation failed"));
@@ -334,7 +334,7 @@ lbw_status lbw_create_grid(const lbw_grid_desc* desc, void* stream, lbw_grid** o
     src = tf.data();
   }
   e = cudaMemcpyAsync(g->table, src, tbytes, cudaMemcpyHostToDevice, g->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g->counters, 0, 4 * sizeof(unsigned long long), g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->counters, 0, 5 * sizeof(unsigned long long), g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->f[0], 0, fbytes, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "create: upload"));
@@ -378,7 +378,7 @@ lbw_status lbw_init(lbw_grid* g, const lbw_pulse* host_pulses, int32_t n_pulses)
   cudaError_t e = cudaMemcpyAsync(d_p, hp.data(), pb, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = launch_init(g, d_p, n_pulses);
   cudaFreeAsync(d_p, g->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g->counters, 0, 4 * sizeof(unsigned long long), g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->counters, 0, 5 * sizeof(unsigned long long), g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_fail(e, "init");
   g->steps = 0;
@@ -410,6 +410,17 @@ lbw_status lbw_step(lbw_grid* g, int64_t n_steps) {
     --left;
   }
   g->steps += n_steps;
+  return LBW_OK;
+}
+
+lbw_status lbw_inject_wait_timeout(lbw_grid* g) {
+  if (!g) return fail(LBW_EINVAL, "grid is NULL");
+  if (!g->initialised) return fail(LBW_ESTATE, "lbw_inject_wait_timeout before lbw_init");
+  if (g->tma_by == 0)
+    return fail(LBW_EINVAL, "this lattice runs the register-pipelined step kernel, which has no device waits");
+  // any non-zero value requests the injected timeout; lbw_init clears it
+  LBW_CUDA(cudaMemsetAsync(g->counters + 4, 0xff, sizeof(unsigned long long), g->stream));
+  LBW_CUDA(cudaStreamSynchronize(g->stream));
   return LBW_OK;
 }
 

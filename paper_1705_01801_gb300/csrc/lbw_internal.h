@@ -42,7 +42,8 @@ struct Grid {
   int32_t* probe_q = nullptr;     // device, nprobe x 3
   double* series = nullptr;       // device, nprobe x cap
   int64_t cap = 0;
-  // device counters: [0] steps since init, [1] samples recorded, [2] last-block ticket
+  // device counters: [0] steps since init, [1] samples recorded, [2] last-block ticket,
+  // [3] timeout flag of a bounded wait, [4] injected-timeout request (tests)
   unsigned long long* counters = nullptr;
   int64_t steps = 0;       // host mirror of counters[0]
   bool initialised = false;

@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
   __shared__ int probe_list[kMaxProbes];
   __shared__ int probe_cnt;
   __shared__ int abort_flag;
+  __shared__ int stall_req;
   __shared__ unsigned long long t_sample;
 
   // Programmatic dependent launch: this grid may be scheduled while the previous step drains;
@@ -134,15 +135,19 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
   const unsigned SL = OFF + 128, RHO = SL + NB * SLOTB, TAB = RHO + RHOB;
   auto full_at = [&](int k) { return sbase + OFF + 8u * k; };
   auto empty_at = [&](int k) { return sbase + OFF + 8u * (NB + k); };
+  // a barrier that no thread or copy ever completes: the target of the injected timeout
+  const unsigned stall_bar = sbase + OFF + 8u * (2 * NB);
 
   if (tid == 0) {
     for (int k = 0; k < NB; ++k) {
       mbar_init_count(full_at(k), 1);
       mbar_init_count(empty_at(k), NCW);
     }
+    mbar_init_count(stall_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     probe_cnt = 0;
     abort_flag = 0;
+    stall_req = a.counters[4] != 0ull;  // failure injection (lbw_inject_wait_timeout)
     t_sample = a.counters[1];
   }
   __syncthreads();
@@ -153,10 +158,15 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
   }
   __syncthreads();
 
-  auto wait_bar = [&](unsigned bar, unsigned parity) -> bool {
+  // Bounded wait for a phase of `bar`: after `limit` tries the CTA's abort flag and the step's
+  // timeout flag (counters[3]) are raised.  With `watch`, the wait also gives up (raising
+  // nothing) as soon as another warp of the CTA has raised the abort flag.
+  auto wait_bar = [&](unsigned bar, unsigned parity, long long limit = kWaitLimit,
+                      bool watch = false) -> bool {
     long long it = 0;
     while (!mbar_try_wait(bar, parity)) {
-      if (++it > kWaitLimit) {
+      if (watch && *reinterpret_cast<volatile int*>(&abort_flag)) return false;
+      if (++it > limit) {
         abort_flag = 1;
         a.counters[3] = 1;
         return false;
@@ -175,7 +185,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       int s = 0, use = 0;
       int issued = z0 - 3;
       for (int p = z0 - 2; p <= z1 + (RG ? 0 : 1); ++p) {
-        if (use > 0 && !wait_bar(empty_at(s), (unsigned)((use - 1) & 1))) break;
+        if (use > 0 && !wait_bar(empty_at(s), (unsigned)((use - 1) & 1), kWaitLimit, true)) break;
         const unsigned bar = full_at(s);
         const unsigned base = sbase + SL + s * SLOTB;
         const int pg = resolve(p, a.n3, p3);
@@ -525,62 +535,70 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       }
     };
 
-    // rho of plane z0 - 1 at the own nodes, from the staged planes z0 - 2 (population 5 only),
-    // z0 - 1 and z0; then step A of plane z0
-    // the slot that completes what step A of plane u needs: u's own (RG) or u + 1's
-    constexpr int AHEAD = RG ? 0 : 1;
-    bool ok = wait_bar(full_at(0), 0) && wait_bar(full_at(1), 0) && (RG || wait_bar(full_at(2), 0));
-    if (ok && owner) stepA(z0 - 1, fB, rA, 0, 1, 2, 2, false);
-    if (lane == 0) mbar_arrive(empty_at(0));  // plane z0 - 2 is no longer needed
-    ok = ok && wait_bar(full_at(2 + AHEAD), 0);
-    if (ok) stepA(z0, fA, rB, 1, 2, 3, 0, true);
-    if (lane == 0) mbar_arrive(empty_at(1));  // nor is plane z0 - 1
-    ok = !named_sync_or(1, NCW * 32, !ok || abort_flag);
-    // slots of raw planes z, z + 1, z + 2 (plane z0 - 2 sits in slot 0) and the fill count of
-    // the awaited slot (plane z + 1's or z + 2's), advanced plane by plane.  rho planes rotate
-    // through three buffers: a warp writing plane z + 1's buffer has passed the barrier that
-    // follows every read of that buffer (plane z - 2); the rows of plane z0 - 1 in buffer 2
-    // are never written or read.
-    int sz = 2, s1 = 3, s2 = 4, uw = 0, rbz = 0, rb1 = 1;
-    auto advance = [&]() {
-      rbz = rb1;
-      rb1 = rb1 == 2 ? 0 : rb1 + 1;
-      sz = s1;
-      s1 = s2;
-      s2 = s2 == NB - 1 ? 0 : s2 + 1;
-      if ((RG ? s1 : s2) == 0) ++uw;
-    };
-    // iteration z: raw plane z + 1 (RG) or z + 2 in, A(z + 1), barrier, B(z), release raw
-    // plane z.  Every warp passes the same barriers; the barrier ORs the warps' abort states
-    // (a timed-out wait here, or the producer's flag), so all warps leave after the same
-    // iteration.
-    auto iter = [&](int zz, R (&fc)[7][NPT], R (&fn)[7][NPT], const R (&rp)[NPT],
-                    const R (&rc)[NPT], R (&rn)[NPT], bool collide) {
-      const bool in = wait_bar(full_at(RG ? s1 : s2), (unsigned)(uw & 1));
-      if (in) stepA(zz + 1, fn, rn, sz, s1, s2, rb1, true);
-      const bool go = !named_sync_or(1, NCW * 32, !in || abort_flag);
-      if (go && collide) stepB(zz, fc, rp, rc, rn, sz, rbz);
-      if (lane == 0) mbar_arrive(empty_at(sz));  // raw plane zz is no longer needed
-      advance();
-      return go;
-    };
-    int z = z0;
-    if (!owner) {  // halo rows and rows beyond the lattice: rho only
-      for (; ok && z < z1; ++z) ok = iter(z, fA, fB, rA, rB, rC, false);
+    if (stall_req) {
+      // Injected timeout: every consumer warp waits on the barrier nothing completes, so the
+      // bounded wait runs out and raises the flags.  No slot is consumed or released, hence
+      // the producer never re-fills a slot whose copy may still be in flight; it stops at its
+      // first wait for a released slot and drains the copies it issued.
+      wait_bar(stall_bar, 0, kStallTries);
     } else {
-      for (; ok && z + 1 < z1; z += 2) {
-        ok = iter(z, fA, fB, rA, rB, rC, true);
-        if (!ok) break;
-        ok = iter(z + 1, fB, fA, rB, rC, rA, true);
-        // next pair expects rho(z+1), rho(z+2) in rA, rB
-#pragma unroll
-        for (int k = 0; k < NPT; ++k) {
-          const R t = rA[k];
-          rA[k] = rC[k];
-          rB[k] = t;
+      // rho of plane z0 - 1 at the own nodes, from the staged planes z0 - 2 (population 5 only),
+      // z0 - 1 and z0; then step A of plane z0
+      // the slot that completes what step A of plane u needs: u's own (RG) or u + 1's
+      constexpr int AHEAD = RG ? 0 : 1;
+      bool ok = wait_bar(full_at(0), 0) && wait_bar(full_at(1), 0) && (RG || wait_bar(full_at(2), 0));
+      if (ok && owner) stepA(z0 - 1, fB, rA, 0, 1, 2, 2, false);
+      if (lane == 0) mbar_arrive(empty_at(0));  // plane z0 - 2 is no longer needed
+      ok = ok && wait_bar(full_at(2 + AHEAD), 0);
+      if (ok) stepA(z0, fA, rB, 1, 2, 3, 0, true);
+      if (lane == 0) mbar_arrive(empty_at(1));  // nor is plane z0 - 1
+      ok = !named_sync_or(1, NCW * 32, !ok || abort_flag);
+      // slots of raw planes z, z + 1, z + 2 (plane z0 - 2 sits in slot 0) and the fill count of
+      // the awaited slot (plane z + 1's or z + 2's), advanced plane by plane.  rho planes rotate
+      // through three buffers: a warp writing plane z + 1's buffer has passed the barrier that
+      // follows every read of that buffer (plane z - 2); the rows of plane z0 - 1 in buffer 2
+      // are never written or read.
+      int sz = 2, s1 = 3, s2 = 4, uw = 0, rbz = 0, rb1 = 1;
+      auto advance = [&]() {
+        rbz = rb1;
+        rb1 = rb1 == 2 ? 0 : rb1 + 1;
+        sz = s1;
+        s1 = s2;
+        s2 = s2 == NB - 1 ? 0 : s2 + 1;
+        if ((RG ? s1 : s2) == 0) ++uw;
+      };
+      // iteration z: raw plane z + 1 (RG) or z + 2 in, A(z + 1), barrier, B(z), release raw
+      // plane z.  Every warp passes the same barriers; the barrier ORs the warps' abort states
+      // (a timed-out wait here, or the producer's flag), so all warps leave after the same
+      // iteration.
+      auto iter = [&](int zz, R (&fc)[7][NPT], R (&fn)[7][NPT], const R (&rp)[NPT],
+                      const R (&rc)[NPT], R (&rn)[NPT], bool collide) {
+        const bool in = wait_bar(full_at(RG ? s1 : s2), (unsigned)(uw & 1));
+        if (in) stepA(zz + 1, fn, rn, sz, s1, s2, rb1, true);
+        const bool go = !named_sync_or(1, NCW * 32, !in || abort_flag);
+        if (go && collide) stepB(zz, fc, rp, rc, rn, sz, rbz);
+        if (lane == 0) mbar_arrive(empty_at(sz));  // raw plane zz is no longer needed
+        advance();
+        return go;
+      };
+      int z = z0;
+      if (!owner) {  // halo rows and rows beyond the lattice: rho only
+        for (; ok && z < z1; ++z) ok = iter(z, fA, fB, rA, rB, rC, false);
+      } else {
+        for (; ok && z + 1 < z1; z += 2) {
+          ok = iter(z, fA, fB, rA, rB, rC, true);
+          if (!ok) break;
+          ok = iter(z + 1, fB, fA, rB, rC, rA, true);
+          // next pair expects rho(z+1), rho(z+2) in rA, rB
+  #pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+            const R t = rA[k];
+            rA[k] = rC[k];
+            rB[k] = t;
+          }
         }
+        if (ok && z < z1) ok = iter(z, fA, fB, rA, rB, rC, true);
       }
-      if (ok && z < z1) ok = iter(z, fA, fB, rA, rB, rC, true);
     }
   }
 

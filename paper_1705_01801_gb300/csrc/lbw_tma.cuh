@@ -88,6 +88,7 @@ __device__ __forceinline__ float2 fma2(float2 x, float2 y, float2 z) { return __
 __device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, bc2(-1.f), x); }
 
 constexpr long long kWaitLimit = 1LL << 20;  // x up to 2 us per try: about 2 s
+constexpr long long kStallTries = 256;       // the injected timeout: under a millisecond
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);

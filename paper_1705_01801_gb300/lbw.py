@@ -21,7 +21,7 @@ STATUS_NAMES = ["LBW_OK", "LBW_EINVAL", "LBW_ENOMEM", "LBW_ECUDA", "LBW_EUNSTABL
 # every symbol the header declares (checked by tests/test_abi.py)
 EXPORTS = ["lbw_create_grid", "lbw_init", "lbw_step", "lbw_probe", "lbw_probe_read",
            "lbw_spectrum", "lbw_spectrum_lowest", "lbw_spectrum_series", "lbw_spectrum_series_static", "lbw_get_field", "lbw_get_populations",
-           "lbw_set_populations", "lbw_step_count", "lbw_destroy", "lbw_last_error", "lbw_source",
+           "lbw_set_populations", "lbw_step_count", "lbw_inject_wait_timeout", "lbw_destroy", "lbw_last_error", "lbw_source",
            "lbw_batch_create", "lbw_batch_init", "lbw_batch_probe", "lbw_batch_step", "lbw_batch_source",
            "lbw_batch_probe_read", "lbw_batch_spectrum", "lbw_batch_spectrum_lowest", "lbw_batch_get_populations",
            "lbw_batch_tune", "lbw_batch_info", "lbw_batch_destroy",
@@ -79,6 +79,7 @@ def lib():
                 "lbw_get_populations": (st, [vp, dp]),
                 "lbw_set_populations": (st, [vp, dp]),
                 "lbw_step_count": (st, [vp, ctypes.POINTER(i64)]),
+                "lbw_inject_wait_timeout": (st, [vp]),
                 "lbw_destroy": (None, [vp]),
                 "lbw_last_error": (ctypes.c_char_p, []),
                 "lbw_batch_create": (st, [ctypes.POINTER(lbw_grid_desc), i32, vp, ctypes.POINTER(vp)]),
@@ -250,6 +251,10 @@ def lbw_step_count(grid):
     n = ctypes.c_int64()
     _check(lib().lbw_step_count(grid, ctypes.byref(n)))
     return n.value
+
+
+def lbw_inject_wait_timeout(grid):
+    _check(lib().lbw_inject_wait_timeout(grid))
 
 
 def lbw_destroy(grid):

@@ -99,3 +99,47 @@ def test_torus_checkpoint_round_trip_is_exact():
     f = g.get_f()
     g.set_f(f)
     assert np.array_equal(g.get_f(), f)
+
+
+def test_injected_wait_timeout_is_reported_and_init_recovers():
+    """A step whose bounded device wait runs out (made to happen on purpose: the consumer warps
+    wait on a barrier that nothing completes, for a few hundred tries) raises the timeout flag;
+    the calls that synchronise then return LBW_ETIMEOUT, the GPU stays usable, and lbw_init
+    brings back a state whose run matches the FP64 oracle."""
+    from paper_1705_01801_gb300 import lbw
+    spec = _cyl(PREC_F32, n=(13, 128, 10))  # q2 extent a multiple of the tile width: tile kernel
+    pl = pulses(spec, 4, 1, sigma=2.5, margin=3)
+    pr = probes(spec, 4, 2)
+    g = lbw.Grid(spec)
+    g.init(pl)
+    g.set_probes(pr, 100)
+    g.step(4)
+    g.read_probes()  # no flag before the injection
+    lbw.lbw_inject_wait_timeout(g.handle)
+    g.step(70)  # single launches and one 64-step graph chain
+    for call in (g.read_probes, lambda: g.spectrum(-1, 2), g.get_P, g.get_f):
+        with pytest.raises(lbw.LbwError) as e:
+            call()
+        assert e.value.status == lbw.LBW_ETIMEOUT, str(e.value)
+    g.init(pl)
+    g.set_probes(pr, 80)
+    g.step(80)
+    o = oracle.OracleGrid(spec)
+    o.init(pl)
+    o.set_probes(pr, 80)
+    o.step(80)
+    Pg, Po = g.get_P(), o.get_P()
+    assert np.linalg.norm(Pg - Po) / np.linalg.norm(Po) < 2e-5
+
+
+def test_injected_timeout_needs_the_tile_kernel():
+    from paper_1705_01801_gb300 import lbw
+    spec = _cyl(PREC_F32, n=(13, 40, 10))  # 40 columns: register-pipelined kernel, no waits
+    g = lbw.Grid(spec)
+    with pytest.raises(lbw.LbwError) as e:
+        lbw.lbw_inject_wait_timeout(g.handle)
+    assert e.value.status == lbw.LBW_ESTATE
+    g.init(pulses(spec, 4, 1, sigma=2.5, margin=3))
+    with pytest.raises(lbw.LbwError) as e:
+        lbw.lbw_inject_wait_timeout(g.handle)
+    assert e.value.status == lbw.LBW_EINVAL
