@@ -1,0 +1,81 @@
+"""Parity at the benchmark lattices' stated run lengths, against FP64 oracle runs stored in
+tests/golden/ by tests/golden/make_long_runs.py (which calls only oracle/).
+
+* cylinder 128 x 128 x 256 (8 random-phase pulses, 16 probes) over its full 20 000 steps:
+  the device's FP32 run (the benchmark's storage) must give the oracle's mode frequencies
+  (8 strongest peaks of the summed probes) within 0.1 %, and its field drift stays on the
+  expected FP32 curve: relative L2 <= 1e-5 at 1000 steps, growing about linearly with the
+  step count (coefficient rounding), reported at every checkpoint.  The FP64 run must agree
+  with the oracle to rounding at every checkpoint.
+* torus 192 x 1024 x 256 (1 pulse, 64 probes) over the 500 steps the oracle stores: FP32
+  field within 1e-5, spectra within 0.1 %.
+The field is compared on the 256 seeded nodes the golden files hold.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import lbw_workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "golden"))
+import make_long_runs as G  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(name, prec):
+    """Device run of the workload at `prec`: sampled P at each stored checkpoint, the 8
+    strongest peaks of the summed probes, and the stored oracle results."""
+    from paper_1705_01801_gb300 import lbw
+    steps, peaks, nodes, fields = G.load(name)
+    wl = W.workload(name)
+    spec = wl.spec.with_(prec=prec)
+    g = lbw.Grid(spec)
+    try:
+        g.init(wl.pulses)
+        g.set_probes(wl.probes, steps)
+        done, curve = 0, {}
+        for cp in sorted(fields):
+            g.step(cp - done)
+            done = cp
+            P = g.get_P()
+            got = P[nodes[:, 2], nodes[:, 0], nodes[:, 1]]
+            ref = fields[cp]
+            curve[cp] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        freq, _ = g.spectrum(-1, len(peaks))
+    finally:
+        g.close()
+    return curve, np.asarray(freq), peaks
+
+
+def _peak_rel(freq, peaks):
+    assert len(freq) == len(peaks)
+    return np.abs(freq - peaks[:, 0]) / peaks[:, 0]
+
+
+def test_cylinder_full_length_fp32():
+    curve, freq, peaks = _run("cylinder", W.PREC_F32)
+    print("\ncylinder FP32 field rel-L2 vs FP64 oracle:", {k: f"{v:.2e}" for k, v in curve.items()})
+    print("cylinder FP32 mode frequency rel. error:", np.array2string(_peak_rel(freq, peaks), precision=2))
+    assert curve[1000] <= 1e-5
+    for cp, err in curve.items():  # linear growth of FP32 coefficient rounding, 1e-5 per 1000
+        assert err <= 1e-5 * cp / 1000, (cp, err)
+    assert _peak_rel(freq, peaks).max() <= 1e-3
+
+
+def test_cylinder_full_length_fp64():
+    curve, freq, peaks = _run("cylinder", W.PREC_F64)
+    for cp, err in curve.items():
+        assert err <= 1e-10, (cp, err)
+    assert _peak_rel(freq, peaks).max() <= 1e-8
+
+
+def test_torus_stored_length_fp32():
+    curve, freq, peaks = _run("torus", W.PREC_F32)
+    print("\ntorus FP32 field rel-L2 vs FP64 oracle:", {k: f"{v:.2e}" for k, v in curve.items()})
+    for cp, err in curve.items():
+        assert err <= 1e-5, (cp, err)
+    assert _peak_rel(freq, peaks).max() <= 1e-3

@@ -361,6 +361,28 @@ def test_free_face_in_curved_coordinates_reflects_like_flat_space():
         assert np.min(np.abs(a - w)) < 1e-9, w
 
 
+@pytest.mark.parametrize("c", [0.1, 0.4])
+def test_free_face_on_a_curved_inner_wall_grows(c):
+    """The copy rule keeps the normal derivative of rho = sqrt(g) P at zero.  On an annulus
+    that is (d_r + 1/r) P = 0; at an inner wall (outward normal -r) it reads d_n P = P / r,
+    a Robin condition whose boundary term makes the wave energy indefinite, so the equation
+    has a non-oscillating growing solution (P ~ K0(kr) e^{ckt}).  The step operator shows it:
+    a real eigenvalue above 1 with a free inner wall, while a free outer wall (where the same
+    condition gives d_n P = -P / r, energy-bounding) and the wall rules stay neutrally stable.
+    This is why the driven pipes here use a rigid inner wall where the paper has a free one."""
+    def radius(inner, outer):
+        n = (8, 8, 1)
+        spec = GridSpec(kind=KIND_POLAR, n=n, h=(1.0, 2 * math.pi / n[1], 1), x0=(4.0, 0, 0), c=c,
+                        bc=(inner, outer, 0, 0, 0, 0))
+        ev = np.linalg.eigvals(_step_matrix(spec))
+        k = int(np.argmax(np.abs(ev)))
+        return abs(ev[k]), abs(np.angle(ev[k]))
+    rho, ang = radius(BC_FREE, BC_BOUNCE)
+    assert rho > 1.002 and ang < 1e-9, (rho, ang)
+    for inner, outer in ((BC_BOUNCE, BC_FREE), (BC_BOUNCE, BC_BOUNCE), (BC_ANTIBOUNCE, BC_BOUNCE)):
+        assert radius(inner, outer)[0] < 1 + 1e-9, (inner, outer)
+
+
 def _impedance_reflection(c, D, cs2=0.25):
     """Reflection coefficient of the damped bounce-back wall for the wave equation.  Near the
     wall the populations are their equilibria to first order, f_i ~ w_i (rho + xi_i j / cs2);
