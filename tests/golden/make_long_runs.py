@@ -83,14 +83,14 @@ def run(name):
                  f"{os.environ.get('OMP_NUM_THREADS', os.cpu_count())} host threads\n")
         fh.write(f"peaks {len(freq)}  # freq (rad/step) amp, summed probe series, k = {K_PEAKS}\n")
         for f, a in zip(freq, amp):
-            fh.write(f"{f!r} {a!r}\n")
+            fh.write(f"{float(f)!r} {float(a)!r}\n")
         fh.write(f"samples {len(nodes)} seed {SAMPLE_SEED}  # q1 q2 q3\n")
         for q in nodes:
             fh.write(f"{q[0]} {q[1]} {q[2]}\n")
         for cp, vals in fields:
             fh.write(f"field {cp}  # P at the sampled nodes after {cp} steps\n")
             for v in vals:
-                fh.write(f"{v!r}\n")
+                fh.write(f"{float(v)!r}\n")
 
 
 def load(name):

@@ -73,7 +73,9 @@ def _desc(**kw):
     ({"kind": 3, "horn_profile": 5}, "horn_profile"),
     ({"c": 1.5}, "too coarse"),                      # beyond the stability bound
     ({"x0": (-6.0, 0.0, 0.0)}, "metric undefined"),  # r <= 0 on the lattice
-], ids=["kind", "damping", "prec", "periodic-pair", "angular", "horn", "stability", "metric"])
+    ({"geom_mode": 3}, "geom_mode"),
+], ids=["kind", "damping", "prec", "periodic-pair", "angular", "horn", "stability", "metric",
+        "geom-mode"])
 def test_descriptor_rules_are_checked_on_the_host(fields, message):
     """Every descriptor rule of lbw_create_grid is decided before any CUDA call: the status is
     LBW_EINVAL and the thread's last error names the rule."""

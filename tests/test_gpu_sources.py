@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from lbw_workloads import (BC_BOUNCE, BC_PERIODIC, KIND_CYLINDRICAL, PREC_F32, PREC_F64, GridSpec,
+from lbw_workloads import (BC_BOUNCE, BC_FREE, BC_PERIODIC, KIND_CYLINDRICAL, PREC_F32, PREC_F64, GridSpec,
                            ensemble, pulses, probes)
 from test_gpu_parity import SPECS
 
@@ -115,3 +115,81 @@ def test_resonance_sweep_finds_the_driven_pipe_mode():
     print(f"closed form {theory:.6f}, free-decay mode {mode:.6f}, sweep peak {peak:.6f} rad/step")
     assert abs(peak - mode) < 0.01 * mode
     assert resp.max() > 2 * resp.min()
+
+
+# ---------------------------------------------------------------- the paper's pipe ---------
+
+def _paper_pipe(damping, prec=PREC_F32):
+    """The open-closed pipe of Sec. IV.A: 20 x 5 x 100 cells over r in [1, 25] (h_r = 1.2),
+    z in [0, 100], c = 0.1; bounce-back with damping D at r = 25 and at the closed end z = 0,
+    a free face at the open end z = 100.  The paper's free inner face at r = 1 grows without
+    bound under the copy rule (on a curved inner wall it is a Robin condition with the
+    destabilising sign), so the inner wall is rigid here, with the same D."""
+    n = (20, 5, 100)
+    return GridSpec(kind=KIND_CYLINDRICAL, n=n, h=(1.2, 2 * math.pi / n[1], 1.0), x0=(1.0, 0, 0),
+                    c=0.1, damping=damping, prec=prec,
+                    bc=(BC_BOUNCE, BC_BOUNCE, BC_PERIODIC, BC_PERIODIC, BC_BOUNCE, BC_FREE))
+
+
+PAPER_PROBE = [1, 0, 10]  # r = 2.8, z = 10.5: the paper's probe at r = 3, z = z_max / 10
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["ring", "plate"])
+def test_paper_pipe_sources_match_oracle(kind):
+    """The paper's pipe with D = 0.65, driven by the ring (P at r_min, z = 0) or the plate
+    (J'_z over the cross-section at z = 0): device and FP64 oracle agree."""
+    from paper_1705_01801_gb300 import lbw
+    spec = _paper_pipe(0.65, prec=PREC_F64)
+    src = _ring(spec, 0, 0) if kind == 0 else _plate(spec, 0)
+    g = lbw.Grid(spec)
+    g.init(np.zeros((0, 5)))
+    g.set_sources(src, kind=kind, amp=1.0, omega=0.0123)
+    g.set_probes([PAPER_PROBE], 700)
+    g.step(700)
+    o = oracle.OracleGrid(spec)
+    o.init(np.zeros((0, 5)))
+    o.set_sources(src, kind=kind, amp=1.0, omega=0.0123)
+    o.set_probes([PAPER_PROBE], 700)
+    o.step(700)
+    fo = o.get_f()
+    np.testing.assert_allclose(g.get_f(), fo, rtol=0, atol=1e-11 * np.abs(fo).max())
+    so = o.read_probes()
+    np.testing.assert_allclose(g.read_probes(), so, rtol=0, atol=1e-10 * np.abs(so).max())
+
+
+def test_paper_pipe_is_an_open_closed_pipe():
+    """Free decay of the paper's pipe (lossless walls, a layer of pulses across the section near
+    the closed end, the paper's probe): the lowest modes are the open-closed pipe's plane-wave family, odd
+    multiples (1 : 3 : 5 : 7) of a quarter wave (Sec. IV.A), with the open end at
+    L_e = L - cs^2 / c (the free face's end correction); and the ring-source sweep of the
+    paper's protocol (8400 steps, response = largest |P| at the probe over the last 2000)
+    peaks on them within the sweep's resolution 2 pi / 8400."""
+    from paper_1705_01801_gb300 import lbw, sweep
+    from lbw_workloads import embedding, node_coords
+    spec = _paper_pipe(1.0)
+    g = lbw.Grid(spec)
+    pl = []
+    for i in range(1, spec.n[0], 3):  # nearly uniform across the section: the plane-wave modes
+        for j in range(spec.n[1]):
+            X = embedding(spec, *node_coords(spec, i, j, 3))
+            pl.append([X[0], X[1], X[2], 2.5, 1.0])
+    g.init(pl)
+    T = 65536
+    g.set_probes([PAPER_PROBE], T)
+    g.step(T)
+    f, _ = g.spectrum(0, 6, lowest=True, rel_power=1e-3)
+    f = np.sort(np.asarray(f))
+    L_e = spec.n[2] - spec.cs2 / spec.c
+    quarter = [(2 * n + 1) * math.pi * spec.c / (2 * L_e) for n in range(4)]
+    print("free-decay modes", np.round(f[:5], 6), "quarter-wave family", np.round(quarter, 6))
+    np.testing.assert_allclose(f[:4], quarter, rtol=1e-2)
+    np.testing.assert_allclose(f[1:4] / f[0], [3, 5, 7], rtol=2e-2)
+    omegas = np.linspace(0.0008, 0.0125, 235)
+    resp = sweep.resonance_curve(spec, _ring(spec, 0, 0), PAPER_PROBE, omegas, steps=8400,
+                                 tail=2000, kind=0)
+    peaks = [omegas[k] for k in range(1, len(resp) - 1)
+             if resp[k] > resp[k - 1] and resp[k] >= resp[k + 1] and resp[k] > 2 * np.median(resp)]
+    print("sweep peaks", np.round(peaks, 6))
+    res = 2 * math.pi / 8400
+    for m in f[:4]:
+        assert min(abs(p - m) for p in peaks) < res, (m, peaks)
