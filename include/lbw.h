@@ -80,8 +80,18 @@ typedef struct {
                            1 = exponential s = (a0 + b e^{alpha z}) / (a0 + b) */
   int32_t bc[6];        /* lbw_bc of faces -q1, +q1, -q2, +q2, -q3, +q3 */
   int32_t prec;         /* lbw_prec */
-  int32_t reserved;     /* must be 0 */
+  int32_t geom_mode;    /* lbw_geom_mode: where the step kernel takes the geometry from */
 } lbw_grid_desc;
+
+/* Geometry source of the fused step (Sec. IV: sqrt g, g^{ab} and G^a enter every node's
+ * forcing term through 16 coefficients per (q1, q3) row, the same along q2 for every kind).
+ * TABLE: built once on the host in FP64, rounded to the arithmetic type, staged per plane by
+ * TMA with the populations.  ANALYTIC: recomputed per row and plane inside the step kernel
+ * from the closed-form metric in the arithmetic type (FP32 or FP64), by the producer warp's
+ * lanes; only lattices on the tile kernel (q2 extent a multiple of the tile width,
+ * non-periodic q1) and single lattices (not ensembles) accept it.  AUTO takes the table, the
+ * faster of the two on the benchmark lattices (measured). */
+typedef enum { LBW_GEOM_AUTO = 0, LBW_GEOM_TABLE = 1, LBW_GEOM_ANALYTIC = 2 } lbw_geom_mode;
 
 /* A Gaussian pulse P0 = amp exp(-|X - x|^2 / (2 sigma^2)) in the embedding distance. */
 typedef struct {

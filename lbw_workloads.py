@@ -24,6 +24,7 @@ KIND_CARTESIAN, KIND_POLAR, KIND_CYLINDRICAL, KIND_TRUMPET, KIND_TOROIDAL = rang
 BC_PERIODIC, BC_BOUNCE, BC_ANTIBOUNCE, BC_FREE = range(4)
 PREC_F64, PREC_F32, PREC_F16S, PREC_BF16S = range(4)
 PROFILE_BESSEL, PROFILE_EXP = 0, 1
+GEOM_AUTO, GEOM_TABLE, GEOM_ANALYTIC = range(3)
 
 # Azimuthal lattice speed c / (r h_theta) allowed at the innermost node.  The step operator
 # of every workload kind stays neutrally stable there at c = 0.4 (oracle eigenvalue pins);
@@ -45,6 +46,7 @@ class GridSpec:
     profile: int = 0
     bc: tuple = (BC_PERIODIC,) * 6
     prec: int = PREC_F64
+    geom_mode: int = 0  # lbw_geom_mode of include/lbw.h (the oracle always evaluates the metric)
 
     @property
     def nodes(self) -> int:

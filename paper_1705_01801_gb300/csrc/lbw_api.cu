@@ -117,7 +117,8 @@ lbw_status validate(lbw_grid_desc& d) {
   if (!(d.c > 0.0)) return fail(LBW_EINVAL, "c must be > 0");
   if (!(d.damping > 0.0 && d.damping <= 1.0)) return fail(LBW_EINVAL, "damping must be in (0, 1]");
   if (d.prec < 0 || d.prec > 3) return fail(LBW_EINVAL, "prec must be a lbw_prec value");
-  if (d.reserved != 0) return fail(LBW_EINVAL, "reserved must be 0");
+  if (d.geom_mode < LBW_GEOM_AUTO || d.geom_mode > LBW_GEOM_ANALYTIC)
+    return fail(LBW_EINVAL, "geom_mode must be a lbw_geom_mode value");
   if (d.kind == LBW_TRUMPET && d.horn_profile != 0 && d.horn_profile != 1)
     return fail(LBW_EINVAL, "horn_profile must be 0 (Bessel) or 1 (exponential)");
   for (int k = 0; k < 6; ++k)
@@ -339,6 +340,9 @@ lbw_status lbw_create_grid(const lbw_grid_desc* desc, void* stream, lbw_grid** o
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "create: upload"));
   step_launch_shape(g);
+  if (d.geom_mode == LBW_GEOM_ANALYTIC && g->tma_by == 0)
+    return cleanup(fail(LBW_EINVAL, "geom_mode ANALYTIC needs the tile kernel: q2 extent a multiple of "
+                                    "the tile width (64, or 128 for 16-bit storage) and non-periodic q1"));
   *out = g;
   return LBW_OK;
 }

@@ -41,6 +41,116 @@ template <> struct Store<__nv_bfloat16> {
   __device__ static void st(__nv_bfloat16* p, R v) { *p = __float2bfloat16_rn(v); }
 };
 
+// Closed-form geometry of the lattice for the analytic geometry mode: the metric of Sec. IV in
+// lattice coordinates (x^a = x0^a + (q^a + 1/2) h^a), evaluated in the arithmetic type R.
+template <typename R>
+struct GeomArgs {
+  int kind, profile, analytic;
+  R x0r, x0w, h0, h1, h2;  // r (or x) and the third coordinate's origin, spacings
+  R g0, g1, g2;            // torus R | Bessel horn Zmax, lambda | exponential a0, b, alpha
+  R c2, cs2;
+};
+
+template <typename R>
+struct MetricR {
+  R sg, g11, g22, g33, g13, G1, G3;
+};
+
+// sqrt(g), g^{ab} and the contracted Christoffel symbols G^a at lattice position (q1, q3)
+// (Eqs. MetricCylindrical, CylindricalChr; coordinatesTrumpet, MetricTrumpet with a general
+// flare s(z); CoordinatesTorus, AMetricTorus, AChristoffelTorus), written in lattice units.
+template <typename R>
+__device__ MetricR<R> metric_q(const GeomArgs<R>& G, int q1, int q3) {
+  const R r = G.x0r + (R(q1) + R(0.5)) * G.h0;
+  const R w = G.x0w + (R(q3) + R(0.5)) * G.h2;
+  R sg = 1, g11 = 1, g22 = 1, g33 = 1, g13 = 0, G1 = 0, G3 = 0;
+  if (G.kind == LBW_POLAR || G.kind == LBW_CYLINDRICAL) {
+    sg = r; g22 = R(1) / (r * r); G1 = R(-1) / r;
+  } else if (G.kind == LBW_TRUMPET) {
+    R s, ds, dds;
+    if (G.profile == 0) {
+      const R Z = G.g0 - w, lam = G.g1;
+      s = pow(Z, -lam);
+      ds = lam * s / Z;
+      dds = lam * (lam + R(1)) * s / (Z * Z);
+    } else {
+      const R e = exp(G.g2 * w), A = G.g0 + G.g1;
+      s = (G.g0 + G.g1 * e) / A;
+      ds = G.g1 * G.g2 * e / A;
+      dds = G.g2 * ds;
+    }
+    sg = r * s * s;
+    g11 = (R(1) + r * r * ds * ds) / (s * s);
+    g13 = -r * ds / s;
+    g22 = R(1) / (r * r * s * s);
+    G1 = (r * r * s * dds - R(2) * r * r * ds * ds - R(1)) / (r * s * s);
+  } else if (G.kind == LBW_TOROIDAL) {
+    const R cp = cos(w), Rr = G.g0 + r * cp;
+    sg = r * Rr;
+    g22 = R(1) / (Rr * Rr);
+    g33 = R(1) / (r * r);
+    G1 = -(G.g0 + R(2) * r * cp) / (r * Rr);
+    G3 = sin(w) / (r * Rr);
+  }
+  MetricR<R> m;
+  m.sg = sg * G.h0 * G.h1 * G.h2;
+  m.g11 = g11 / (G.h0 * G.h0);
+  m.g22 = g22 / (G.h1 * G.h1);
+  m.g33 = g33 / (G.h2 * G.h2);
+  m.g13 = g13 / (G.h0 * G.h2);
+  m.G1 = G1 / G.h0;
+  m.G3 = G3 / G.h2;
+  return m;
+}
+
+// The 16 force coefficients (TableSlot) of row (q1, q3), with the same ghost rules as the
+// host-built table: free -> rho copied; bounce-back -> P mirrored; anti-bounce-back -> P
+// mirrored with opposite sign; periodic neighbours wrap; the ghost's metric at the ghost.
+template <typename R>
+__device__ void table_row(const GeomArgs<R>& G, const int (&bc)[6], int n1, int n3, int q1, int q3,
+                          R* out) {
+  const MetricR<R> m = metric_q(G, q1, q3);
+  R e[T_SLOTS];
+#pragma unroll
+  for (int k = 0; k < T_SLOTS; ++k) e[k] = R(0);
+  e[T_H22] = R(0.5) * (G.c2 * m.g22 - G.cs2);
+  e[T_MG1] = -G.c2 * m.G1;
+  e[T_MG3] = -G.c2 * m.G3;
+  e[T_SG] = m.sg;
+  e[T_INVSG] = R(1) / m.sg;
+#pragma unroll
+  for (int nb = 0; nb < 4; ++nb) {
+    const int axis = nb < 2 ? 0 : 2, s = (nb & 1) ? 1 : -1;
+    int p1 = q1 + (axis == 0 ? s : 0), p3 = q3 + (axis == 2 ? s : 0);
+    const int n = axis == 0 ? n1 : n3, pos = axis == 0 ? p1 : p3;
+    const int face = 2 * axis + (s > 0 ? 1 : 0);
+    bool ghost = false;
+    if (pos < 0 || pos >= n) {
+      if (bc[face] == LBW_BC_PERIODIC) {
+        if (axis == 0) p1 = (p1 + n) % n; else p3 = (p3 + n) % n;
+      } else {
+        ghost = true;
+      }
+    }
+    const MetricR<R> mn = metric_q(G, p1, p3);
+    const R K11 = G.c2 * mn.g11 - G.cs2, K13 = G.c2 * mn.g13, K33 = G.c2 * mn.g33 - G.cs2;
+    const R k1 = axis == 0 ? K11 : K13, k3 = axis == 0 ? K13 : K33;
+    if (ghost) {
+      const R self = bc[face] == LBW_BC_FREE ? R(1) : (bc[face] == LBW_BC_BOUNCE ? R(1) : R(-1)) * mn.sg / m.sg;
+      e[T_S1] += R(0.5) * R(s) * k1 * self;
+      e[T_S3] += R(0.5) * R(s) * k3 * self;
+    } else if (axis == 0) {
+      e[s > 0 ? T_A1P : T_A1M] = R(0.5) * k1;
+      e[s > 0 ? T_B13P : T_B13M] = R(0.5) * k3;
+    } else {
+      e[s > 0 ? T_C13P : T_C13M] = R(0.5) * k1;
+      e[s > 0 ? T_C33P : T_C33M] = R(0.5) * k3;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < T_SLOTS; ++k) out[k] = e[k];
+}
+
 template <typename S>
 struct StepArgs {
   using R = typename Store<S>::R;
@@ -64,6 +174,7 @@ struct StepArgs {
   // ghost columns that mirror the periodic wrap)
   int pitch, col0;
   long long ps;
+  GeomArgs<R> geo;  // closed-form geometry (used by the tile kernel in the analytic mode)
 };
 
 __device__ __forceinline__ long long node(int q1, int q2, int q3, int n1, int n2) {

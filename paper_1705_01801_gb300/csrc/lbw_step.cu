@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
 
   if (tid == 0) {
     for (int k = 0; k < NB; ++k) {
-      mbar_init_count(full_at(k), 1);
+      mbar_init_count(full_at(k), a.geo.analytic ? 2 : 1);  // analytic: the producer's rows arrive too
       mbar_init_count(empty_at(k), NCW);
     }
     mbar_init_count(stall_bar, 1);
@@ -176,28 +176,35 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
   };
 
   if (w == ROWS) {  // ------------------------------------------------------------ producer
-    if (lane == 0) {
-      int xl = x0 - V, xr = x0 + BX;
-      const bool hl = xl >= 0 || p2, hr = xr < a.n2 || p2;
-      if (xl < 0) xl += a.n2;
-      if (xr >= a.n2) xr -= a.n2;
-      const unsigned tx_pop = (unsigned)(ROWS * BX * ES) + (hl ? ROWS * 16u : 0u) + (hr ? ROWS * 16u : 0u);
-      int s = 0, use = 0;
-      int issued = z0 - 3;
-      for (int p = z0 - 2; p <= z1 + (RG ? 0 : 1); ++p) {
-        if (use > 0 && !wait_bar(empty_at(s), (unsigned)((use - 1) & 1), kWaitLimit, true)) break;
-        const unsigned bar = full_at(s);
-        const unsigned base = sbase + SL + s * SLOTB;
-        const int pg = resolve(p, a.n3, p3);
-        if constexpr (!RG) {  // whole planes
+    // Lane 0 issues the copies.  In the analytic geometry mode every lane of the warp waits for
+    // the slot, lanes 0 .. BY - 1 write the coefficient rows of a collided plane into the
+    // slot's table block, and lane 0 adds the slot's second arrival once they are written.
+    const bool ana = a.geo.analytic != 0;
+    int xl = x0 - V, xr = x0 + BX;
+    const bool hl = xl >= 0 || p2, hr = xr < a.n2 || p2;
+    if (xl < 0) xl += a.n2;
+    if (xr >= a.n2) xr -= a.n2;
+    const unsigned tx_pop = (unsigned)(ROWS * BX * ES) + (hl ? ROWS * 16u : 0u) + (hr ? ROWS * 16u : 0u);
+    const unsigned tab_tx = ana ? 0u : (unsigned)(BY * T_SLOTS * RS);
+    int s = 0, use = 0;
+    int issued = z0 - 3;
+    for (int p = z0 - 2; p <= z1 + (RG ? 0 : 1); ++p) {
+      const bool free_slot = use == 0 || wait_bar(empty_at(s), (unsigned)((use - 1) & 1), kWaitLimit, true);
+      if (!__all_sync(0xffffffffu, free_slot)) break;
+      const unsigned bar = full_at(s);
+      const unsigned base = sbase + SL + s * SLOTB;
+      const int pg = resolve(p, a.n3, p3);
+      bool tab = false;  // this plane is collided here: its coefficient rows ride in the slot
+      if constexpr (!RG) {  // whole planes
+        tab = pg >= 0 && p != z0 - 2 && p >= z0 && p < z1;
+        if (lane == 0) {
           if (pg < 0) {
             mbar_expect_tx(bar, 0);
           } else if (p == z0 - 2) {  // only population 5 of this plane streams into the segment
             mbar_expect_tx(bar, (unsigned)(ROWS * BX * ES));
             tma_load_4d(base + 5 * POPB, &tm_main, x0, y0 - 1, pg, 5, bar);
           } else {
-            const bool tab = p >= z0 && p < z1;
-            mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
+            mbar_expect_tx(bar, 7 * tx_pop + (tab ? tab_tx : 0u));
 #pragma unroll 1
             for (int i = 0; i < 7; ++i) {
               const int row = y0 - 1 - xi1_of(i);
@@ -205,11 +212,13 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
               if (hl) tma_load_4d(base + i * POPB + MB, &tm_halo, xl, row, pg, i, bar);
               if (hr) tma_load_4d(base + i * POPB + MB + HB, &tm_halo, xr, row, pg, i, bar);
             }
-            if (tab) tma_load_3d(sbase + TAB + s * TABB, &tm_tab, 0, y0, pg, bar);
+            if (tab && !ana) tma_load_3d(sbase + TAB + s * TABB, &tm_tab, 0, y0, pg, bar);
           }
-        } else if (p == z0 - 2) {
-          // only population 5 of this plane streams into the segment; when the first pulled
-          // plane z0 - 1 is the q3 = 0 face of a wall, its reflected population 6 rides here
+        }
+      } else if (p == z0 - 2) {
+        // only population 5 of this plane streams into the segment; when the first pulled
+        // plane z0 - 1 is the q3 = 0 face of a wall, its reflected population 6 rides here
+        if (lane == 0) {
           const int pn = (!p3 && z0 == 1) ? 0 : -1;
           mbar_expect_tx(bar, (pg < 0 ? 0u : (unsigned)(ROWS * BX * ES)) + (pn >= 0 ? tx_pop : 0u));
           if (pg >= 0) tma_load_4d(base + 5 * POPB, &tm_main, x0, y0 - 1, pg, 5, bar);
@@ -218,13 +227,14 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
             if (hl) tma_load_4d(base + 6 * POPB + MB, &tm_halo, xl, y0 - 1, pn, 6, bar);
             if (hr) tma_load_4d(base + 6 * POPB + MB + HB, &tm_halo, xr, y0 - 1, pn, 6, bar);
           }
-        } else {
-          // populations 0-5 of plane p and population 6 of plane p + 1 (which streams into
-          // plane p), so a pulled plane needs its own slot and the one before it only
+        }
+      } else {
+        // populations 0-5 of plane p and population 6 of plane p + 1 (which streams into
+        // plane p), so a pulled plane needs its own slot and the one before it only
+        tab = pg >= 0 && p >= z0 && p < z1;
+        if (lane == 0) {
           const int pn = resolve(p + 1, a.n3, p3);
-          const bool tab = pg >= 0 && p >= z0 && p < z1;
-          mbar_expect_tx(bar, (pg >= 0 ? 6 * tx_pop : 0u) + (pn >= 0 ? tx_pop : 0u) +
-                                  (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
+          mbar_expect_tx(bar, (pg >= 0 ? 6 * tx_pop : 0u) + (pn >= 0 ? tx_pop : 0u) + (tab ? tab_tx : 0u));
 #pragma unroll 1
           for (int i = 0; i < 7; ++i) {
             const int pi = i == 6 ? pn : pg;
@@ -234,17 +244,31 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
             if (hl) tma_load_4d(base + i * POPB + MB, &tm_halo, xl, row, pi, i, bar);
             if (hr) tma_load_4d(base + i * POPB + MB + HB, &tm_halo, xr, row, pi, i, bar);
           }
-          if (tab) tma_load_3d(sbase + TAB + s * TABB, &tm_tab, 0, y0, pg, bar);
+          if (tab && !ana) tma_load_3d(sbase + TAB + s * TABB, &tm_tab, 0, y0, pg, bar);
         }
-        issued = p;
-        if (++s == NB) { s = 0; ++use; }
       }
-      // drain: the last NB staged planes have landed before the CTA exits (bounded)
+      if (ana) {
+        if (tab && lane < BY) {
+          R* rowp = reinterpret_cast<R*>(smem_raw + TAB + s * TABB) + lane * T_SLOTS;
+          if (y0 + lane < a.n1) {
+            table_row(a.geo, a.bc, a.n1, a.n3, y0 + lane, pg, rowp);
+          } else {
+#pragma unroll
+            for (int k = 0; k < T_SLOTS; ++k) rowp[k] = R(0);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar);  // the rows are written (second arrival of the phase)
+      }
+      issued = p;
+      if (++s == NB) { s = 0; ++use; }
+    }
+    // drain: the last NB staged planes have landed before the CTA exits (bounded)
+    if (lane == 0)
       for (int p = max(z0 - 2, issued - NB + 1); p <= issued; ++p) {
         const int k = p - (z0 - 2);
         wait_bar(full_at(k % NB), (unsigned)((k / NB) & 1));
       }
-    }
   } else {  // ------------------------------------------------------------------- consumers
     const int q1 = y0 - 1 + w;
     const bool interior = w >= 1 && w <= BY;
@@ -645,6 +669,19 @@ StepArgs<S> make_args(Grid* g, int src) {
   a.pitch = g->pitch ? g->pitch : g->d.n[1];
   a.col0 = g->col0;
   a.ps = pop_stride(g);
+  a.geo.kind = g->d.kind;
+  a.geo.profile = g->d.horn_profile;
+  a.geo.analytic = g->d.geom_mode == LBW_GEOM_ANALYTIC && g->tma_by > 0;
+  a.geo.x0r = (R)g->d.x0[0];
+  a.geo.x0w = (R)g->d.x0[2];
+  a.geo.h0 = (R)g->d.h[0];
+  a.geo.h1 = (R)g->d.h[1];
+  a.geo.h2 = (R)g->d.h[2];
+  a.geo.g0 = (R)g->d.geom[0];
+  a.geo.g1 = (R)g->d.geom[1];
+  a.geo.g2 = (R)g->d.geom[2];
+  a.geo.c2 = (R)(g->d.c * g->d.c);
+  a.geo.cs2 = (R)g->d.cs2;
   return a;
 }
 

@@ -36,7 +36,7 @@ class lbw_grid_desc(ctypes.Structure):
                 ("cs2", ctypes.c_double), ("damping", ctypes.c_double),
                 ("geom", ctypes.c_double * 4), ("horn_profile", ctypes.c_int32),
                 ("bc", ctypes.c_int32 * 6), ("prec", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("geom_mode", ctypes.c_int32)]
 
 
 class lbw_pulse(ctypes.Structure):
@@ -153,7 +153,7 @@ def make_desc(spec) -> lbw_grid_desc:
     for k in range(6):
         d.bc[k] = int(spec.bc[k])
     d.prec = spec.prec
-    d.reserved = 0
+    d.geom_mode = int(getattr(spec, "geom_mode", 0))
     return d
 
 
