@@ -99,10 +99,11 @@ class OracleGrid:
 
     def __init__(self, spec):
         self.spec = spec
-        ints = np.array([spec.kind, *spec.n, *spec.bc, spec.profile], dtype=np.int32)
+        ints = np.array([spec.kind, *spec.n, *spec.bc, spec.profile,
+                         getattr(spec, "equilibrium", 0)], dtype=np.int32)
         dbls = np.array([*spec.h, *spec.x0, spec.c, spec.cs2, spec.damping, *spec.geom],
                         dtype=np.float64)
-        assert ints.size == 11 and dbls.size == 13
+        assert ints.size == 12 and dbls.size == 13
         self._L = lib()
         self._h = self._L.lbwo_create(_ip(ints), _dp(dbls))
         self.n = tuple(spec.n)

@@ -79,8 +79,12 @@
 #define FACE_ANTIBOUNCE 2
 #define FACE_FREE 3
 
+#define EQ_CURVILINEAR 0
+#define EQ_MOMENT_MATCHING 1
+#define EQ_HERMITE 2
+
 typedef struct {
-  int kind, profile;
+  int kind, profile, eq;
   int n[3];
   int bc[6];
   double h[3], x0[3];
@@ -206,7 +210,7 @@ static long long nid(const OGrid *g, int q1, int q2, int q3) {
 
 /* ---- public (ctypes) interface ------------------------------------------------------- */
 
-/* ints: kind, n1, n2, n3, bc[6], profile   (11 values)
+/* ints: kind, n1, n2, n3, bc[6], profile, equilibrium   (12 values)
  * dbls: h[3], x0[3], c, cs2, damping, gp[4] (13 values) */
 void *lbwo_create(const int32_t *ints, const double *dbls) {
   OGrid *g = (OGrid *)calloc(1, sizeof(OGrid));
@@ -214,6 +218,7 @@ void *lbwo_create(const int32_t *ints, const double *dbls) {
   for (int a = 0; a < 3; a++) g->n[a] = ints[1 + a];
   for (int k = 0; k < 6; k++) g->bc[k] = ints[4 + k];
   g->profile = ints[10];
+  g->eq = ints[11];
   for (int a = 0; a < 3; a++) {
     g->h[a] = dbls[a];
     g->x0[a] = dbls[3 + a];
@@ -317,6 +322,33 @@ static void force(const OGrid *g, const int q[3], double rho, const double G[3],
   for (int a = 0; a < 3; a++) F[a] = -c2 * rho * G[a] - divA[a];
 }
 
+/* The Cartesian schemes that Sec. II compares (flat space, lattice units, no forcing term),
+ * with P = sum_i f_i and J = sum_i f_i xi_i (Eq. MacroscopicQuantities):
+ *   moment matching (Chopard, Eq. feqMomentMatchingCartesian):
+ *     f_0 = P + (c^2 / cs^2) P (w_0 - 1),  f_i = (w_i / cs^2)(c^2 P + xi_i . J);
+ *   Hermite (Eq. EquilibriumHermite, discretised from the Gaussian of Eq. continuousfeq):
+ *     f_i = w_i [P + xi_i . J / cs^2 + P (c^2 - cs^2)(|xi_i|^2 - 3 cs^2) / (2 cs^4)],
+ *     f_0 = P - sum_{i >= 1} f_i (the paper's own rule for the rest population). */
+static void cartesian_feq(const OGrid *g, double P, const double J[3], double feq[7]) {
+  const double cs2 = g->cs2, c2 = g->c * g->c, w0 = 1.0 - 3.0 * cs2, w1 = 0.5 * cs2;
+  if (g->eq == EQ_MOMENT_MATCHING) {
+    feq[0] = P + (c2 / cs2) * P * (w0 - 1.0);
+    for (int i = 1; i < 7; i++) {
+      double xj = XI[i][0] * J[0] + XI[i][1] * J[1] + XI[i][2] * J[2];
+      feq[i] = (w1 / cs2) * (c2 * P + xj);
+    }
+  } else {
+    double rest = P;
+    for (int i = 1; i < 7; i++) {
+      double xj = XI[i][0] * J[0] + XI[i][1] * J[1] + XI[i][2] * J[2];
+      double xi2 = (double)(XI[i][0] * XI[i][0] + XI[i][1] * XI[i][1] + XI[i][2] * XI[i][2]);
+      feq[i] = w1 * (P + xj / cs2 + P * (c2 - cs2) * (xi2 - 3.0 * cs2) / (2.0 * cs2 * cs2));
+      rest -= feq[i];
+    }
+    feq[0] = rest;
+  }
+}
+
 static void record_probes(OGrid *g) {
   if (g->nprobe <= 0 || g->nrec >= g->cap) return;
   for (int k = 0; k < g->nprobe; k++) {
@@ -357,6 +389,13 @@ static void apply_sources(OGrid *g, double *f) {
       for (int i = 0; i < 7; i++) rho += f[i * g->nn + x];
       j3 = sg * v;
     }
+    if (g->eq != EQ_CURVILINEAR) { /* the scheme's own equilibrium carries the imposed value */
+      const double J[3] = {0.0, 0.0, j3};
+      double feq[7];
+      cartesian_feq(g, rho, J, feq);
+      for (int i = 0; i < 7; i++) f[i * g->nn + x] = feq[i];
+      continue;
+    }
     for (int i = 0; i < 7; i++)
       f[i * g->nn + x] = (i == 0) ? w0 * rho : w1 * (rho + XI[i][2] * j3 / cs2);
   }
@@ -391,11 +430,17 @@ static void one_step(OGrid *g) {
         double f[7];
         for (int i = 0; i < 7; i++) f[i] = g->fpull[i * g->nn + x];
         double rho = g->rho[x];
+        double m[3] = {f[1] - f[2], f[3] - f[4], f[5] - f[6]};
+        if (g->eq != EQ_CURVILINEAR) { /* Sec. II schemes: P = rho, J = m, no forcing term */
+          double feq[7];
+          cartesian_feq(g, rho, m, feq);
+          for (int i = 0; i < 7; i++) g->fnew[i * g->nn + x] = 2.0 * feq[i] - f[i];
+          continue;
+        }
         double sg, gi[3][3], G[3];
         geom_q(g, q1, q2, q3, &sg, gi, G);
         double F[3];
         force(g, q, rho, G, F);
-        double m[3] = {f[1] - f[2], f[3] - f[4], f[5] - f[6]};
         double jp[3];
         for (int a = 0; a < 3; a++) jp[a] = m[a] + 0.5 * F[a];
         for (int i = 0; i < 7; i++) {
@@ -445,8 +490,15 @@ void lbwo_init(void *p, const double *pulses, int npulse) {
         int q[3] = {q1, q2, q3};
         long long x = nid(g, q1, q2, q3);
         double sg, gi[3][3], G[3], F[3];
-        geom_q(g, q1, q2, q3, &sg, gi, G);
         double rho0 = g->rho[x];
+        if (g->eq != EQ_CURVILINEAR) { /* at rest: J = 0, no forcing term */
+          const double J0[3] = {0.0, 0.0, 0.0};
+          double feq[7];
+          cartesian_feq(g, rho0, J0, feq);
+          for (int i = 0; i < 7; i++) g->f[i * g->nn + x] = feq[i];
+          continue;
+        }
+        geom_q(g, q1, q2, q3, &sg, gi, G);
         force(g, q, rho0, G, F);
         for (int i = 0; i < 7; i++) {
           double xj = 0.5 * (XI[i][0] * F[0] + XI[i][1] * F[1] + XI[i][2] * F[2]);

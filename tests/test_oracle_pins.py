@@ -123,15 +123,17 @@ def test_paper_christoffels_cylinder_and_torus():
 
 # ---------------------------------------------------------------- flat space --------------
 
-def _plane_wave_omega(c, N, axis, cs2=0.25, steps=4000):
+def _plane_wave_omega(c, N, axis, cs2=0.25, steps=4000, equilibrium=0):
     n = [1, 1, 1]
     n[axis] = N
-    spec = GridSpec(kind=KIND_CARTESIAN, n=tuple(n), h=(1, 1, 1), x0=(0, 0, 0), c=c, cs2=cs2)
+    spec = GridSpec(kind=KIND_CARTESIAN, n=tuple(n), h=(1, 1, 1), x0=(0, 0, 0), c=c, cs2=cs2,
+                    equilibrium=equilibrium)
     g = oracle.OracleGrid(spec)
     k = 2 * math.pi / N
     x = np.arange(N) + 0.5
     shape = {0: (1, N, 1), 1: (1, 1, N), 2: (N, 1, 1)}[axis]  # state is (N3, N1, N2)
     rho = np.cos(k * x).reshape(shape)
+    g.init(np.zeros((0, 5)))
     g.set_f(state_from_rho(rho, cs2))
     g.set_probes([[0, 0, 0]], steps)
     g.step(steps)
@@ -204,6 +206,101 @@ def test_identity_metric_reduces_to_cartesian_wave_lbm():
     for _ in range(12):
         ref = _textbook_wave_lbm_step(ref, cs2)
     np.testing.assert_allclose(g.get_f(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+# ---------------------------------------------------------------- Cartesian schemes (Sec. II)
+
+@pytest.mark.parametrize("c", [0.3, 0.55])
+@pytest.mark.parametrize("axis", [0, 2])
+def test_moment_matching_equilibrium_wave_speed(c, axis):
+    """Chopard's equilibrium (Eq. feqMomentMatchingCartesian) has the stress
+    sum f^eq xi xi = c^2 P delta (Eq. Stress) for any c, so a plane wave runs at c."""
+    om, ck = _plane_wave_omega(c, 64, axis, equilibrium=1)
+    assert abs(om / ck - 1) < 3e-3
+
+
+@pytest.mark.parametrize("c,cs2", [(0.4, 0.25), (0.3, 0.25), (0.4, 0.2)])
+def test_hermite_equilibrium_wave_speed(c, cs2):
+    """The truncated Hermite equilibrium of Eq. EquilibriumHermite, summed with the D3Q7
+    weights (sum w xi xi = cs^2 delta, |xi| = 1), has the stress
+    [cs^2 + (c^2 - cs^2)(1 - 3 cs^2) / (2 cs^2)] P delta: a plane wave runs at that speed,
+    which is c only at cs^2 = 1/5."""
+    c_eff = math.sqrt(cs2 + (c * c - cs2) * (1 - 3 * cs2) / (2 * cs2))
+    om, ck = _plane_wave_omega(c, 64, 0, cs2=cs2, equilibrium=2)
+    assert abs(om / (ck * c_eff / c) - 1) < 3e-3
+    if cs2 == 0.2:
+        assert c_eff == pytest.approx(c, rel=1e-12)
+    else:
+        assert abs(c_eff / c - 1) > 0.05
+
+
+@pytest.mark.parametrize("equilibrium", [1, 2])
+def test_cartesian_equilibria_at_c_equal_cs_are_the_textbook_lbm(equilibrium):
+    """At c = cs both Sec. II equilibria reduce to w_i (P + xi . J / cs^2): the plain wave LBM."""
+    cs2 = 0.25
+    spec = GridSpec(kind=KIND_CARTESIAN, n=(5, 6, 7), h=(1, 1, 1), x0=(0, 0, 0), c=0.5, cs2=cs2,
+                    equilibrium=equilibrium)
+    g = oracle.OracleGrid(spec)
+    g.init(np.zeros((0, 5)))
+    f = np.random.default_rng(9).normal(size=(7, 7, 5, 6))
+    g.set_f(f)
+    g.step(12)
+    ref = f
+    for _ in range(12):
+        ref = _textbook_wave_lbm_step(ref, cs2)
+    np.testing.assert_allclose(g.get_f(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def _point_source_fit(equilibrium, c, cs2, lam=10.0, T=80, N=100):
+    """Sec. II's benchmark: a point source P = sin(omega t), omega = 2 pi c / lambda, at the
+    centre of a 100 x 100 x 1 plane.  The field at time T (before any echo) is an outgoing
+    cylindrical wave, a J0(kr) + b Y0(kr) at each instant; returns the relative RMS residual
+    of that fit with k = omega / c, and the k of best fit over 0.5 .. 1.5 omega / c, as a
+    ratio to omega / c."""
+    from scipy.special import j0, y0
+    spec = GridSpec(kind=KIND_CARTESIAN, n=(N, N, 1), h=(1, 1, 1), x0=(0, 0, 0), c=c, cs2=cs2,
+                    equilibrium=equilibrium,
+                    bc=(BC_ANTIBOUNCE, BC_ANTIBOUNCE, BC_ANTIBOUNCE, BC_ANTIBOUNCE, 0, 0))
+    g = oracle.OracleGrid(spec)
+    g.init(np.zeros((0, 5)))
+    k = 2 * math.pi / lam
+    s = N // 2
+    g.set_sources([[s, s, 0]], kind=0, amp=1.0, omega=c * k)
+    g.step(T)
+    P = g.get_P()[0]
+    q1, q2 = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    r = np.hypot(q1 - s, q2 - s)
+    sel = (r >= 5) & (r <= 0.8 * c * T)
+
+    def resid(kk):
+        A = np.stack([j0(kk * r[sel]), y0(kk * r[sel])], 1)
+        coef, *_ = np.linalg.lstsq(A, P[sel], rcond=None)
+        return math.sqrt(((P[sel] - A @ coef) ** 2).mean() / (P[sel] ** 2).mean())
+
+    ks = np.linspace(0.5 * k, 1.5 * k, 201)
+    return resid(k), ks[int(np.argmin([resid(kk) for kk in ks]))] / k
+
+
+@pytest.mark.parametrize("equilibrium", [0, 1], ids=["curvilinear", "moment-matching"])
+def test_point_source_radiates_at_c(equilibrium):
+    """The paper's method (identity metric) and Chopard's equilibrium radiate the cylindrical
+    wave of the wave equation from a point source: the J0 / Y0 profile at k = omega / c fits
+    to < 8 % (the 2-D lattice's anisotropy and dispersion at ten cells per wavelength) and the
+    best-fit wavenumber is omega / c to 2 %."""
+    e, kr = _point_source_fit(equilibrium, 0.4, 0.25)
+    assert e < 0.08 and abs(kr - 1) < 0.02, (e, kr)
+
+
+def test_point_source_hermite_runs_at_its_stress_speed():
+    """The printed Hermite equilibrium with cs^2 = 1/4 and c = 0.4 radiates at
+    c_eff = sqrt(cs^2 + (c^2 - cs^2)(1 - 3 cs^2) / (2 cs^2)) = 0.453, so its wavefronts have
+    k = omega / c_eff, 12 % shorter than omega / c; at cs^2 = 1/5 it radiates at c."""
+    c, cs2 = 0.4, 0.25
+    c_eff = math.sqrt(cs2 + (c * c - cs2) * (1 - 3 * cs2) / (2 * cs2))
+    _, kr = _point_source_fit(2, c, cs2)
+    assert abs(kr - c / c_eff) < 0.02, (kr, c / c_eff)
+    _, kr = _point_source_fit(2, c, 0.2)
+    assert abs(kr - 1) < 0.02, kr
 
 
 def test_ring_source_radiates_cylindrical_wave():
