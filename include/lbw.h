@@ -81,7 +81,21 @@ typedef struct {
   int32_t bc[6];        /* lbw_bc of faces -q1, +q1, -q2, +q2, -q3, +q3 */
   int32_t prec;         /* lbw_prec */
   int32_t geom_mode;    /* lbw_geom_mode: where the step kernel takes the geometry from */
+  int32_t equilibrium;  /* lbw_equilibrium */
+  int32_t reserved;     /* must be 0 */
 } lbw_grid_desc;
+
+/* Equilibrium of the collision.  CURVILINEAR is the paper's method (Sec. III: the Hermite
+ * equilibrium at c = cs plus the geometric forcing term, Eqs. JCorrectionForce and
+ * EquilibriumCurvedSystemHermiteCorrected), valid for every kind.  The two Cartesian schemes
+ * that Sec. II compares (LBW_CARTESIAN only, FP32 or FP64 storage, table geometry):
+ * MOMENT_MATCHING is Chopard's equilibrium (Eq. feqMomentMatchingCartesian),
+ * f_0 = P (1 - (c^2 / cs^2)(1 - w_0)), f_i = (w_i / cs^2)(c^2 P + xi_i . J), whose stress is
+ * c^2 P delta for any c; HERMITE is the truncated Hermite equilibrium of Eq. EquilibriumHermite,
+ * f_i = w_i [P + xi_i . J / cs^2 + P (c^2 - cs^2)(|xi_i|^2 - 3 cs^2) / (2 cs^4)], f_0 = P - sum
+ * of the others, whose wave speed on D3Q7 is c only at cs^2 = 1/5 (in general c_eff^2 =
+ * cs^2 + (c^2 - cs^2)(1 - 3 cs^2) / (2 cs^2)).  Neither uses a forcing term. */
+typedef enum { LBW_EQ_CURVILINEAR = 0, LBW_EQ_MOMENT_MATCHING = 1, LBW_EQ_HERMITE = 2 } lbw_equilibrium;
 
 /* Geometry source of the fused step (Sec. IV: sqrt g, g^{ab} and G^a enter every node's
  * forcing term through 16 coefficients per (q1, q3) row, the same along q2 for every kind).

@@ -25,6 +25,7 @@ BC_PERIODIC, BC_BOUNCE, BC_ANTIBOUNCE, BC_FREE = range(4)
 PREC_F64, PREC_F32, PREC_F16S, PREC_BF16S = range(4)
 PROFILE_BESSEL, PROFILE_EXP = 0, 1
 GEOM_AUTO, GEOM_TABLE, GEOM_ANALYTIC = range(3)
+EQ_CURVILINEAR, EQ_MOMENT_MATCHING, EQ_HERMITE = range(3)
 
 # Azimuthal lattice speed c / (r h_theta) allowed at the innermost node.  The step operator
 # of every workload kind stays neutrally stable there at c = 0.4 (oracle eigenvalue pins);
@@ -47,6 +48,7 @@ class GridSpec:
     bc: tuple = (BC_PERIODIC,) * 6
     prec: int = PREC_F64
     geom_mode: int = 0  # lbw_geom_mode of include/lbw.h (the oracle always evaluates the metric)
+    equilibrium: int = 0  # lbw_equilibrium: 0 the paper's method, 1 / 2 the Cartesian schemes
 
     @property
     def nodes(self) -> int:

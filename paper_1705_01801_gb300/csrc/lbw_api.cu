@@ -119,6 +119,22 @@ lbw_status validate(lbw_grid_desc& d) {
   if (d.prec < 0 || d.prec > 3) return fail(LBW_EINVAL, "prec must be a lbw_prec value");
   if (d.geom_mode < LBW_GEOM_AUTO || d.geom_mode > LBW_GEOM_ANALYTIC)
     return fail(LBW_EINVAL, "geom_mode must be a lbw_geom_mode value");
+  if (d.reserved != 0) return fail(LBW_EINVAL, "reserved must be 0");
+  if (d.geom_mode == LBW_GEOM_ANALYTIC && d.prec != LBW_F64 && d.prec != LBW_F32)
+    return fail(LBW_EINVAL, "geom_mode ANALYTIC is built for FP32 and FP64 storage");
+  if (d.equilibrium < LBW_EQ_CURVILINEAR || d.equilibrium > LBW_EQ_HERMITE)
+    return fail(LBW_EINVAL, "equilibrium must be a lbw_equilibrium value");
+  if (d.equilibrium != LBW_EQ_CURVILINEAR &&
+      (d.kind != LBW_CARTESIAN || (d.prec != LBW_F64 && d.prec != LBW_F32) || d.geom_mode == LBW_GEOM_ANALYTIC))
+    return fail(LBW_EINVAL, "the moment-matching and Hermite equilibria are the Cartesian schemes of Sec. II: "
+                            "kind CARTESIAN, FP32 or FP64 storage, table geometry");
+  if (d.equilibrium != LBW_EQ_CURVILINEAR) {
+    double E, two0;
+    equilibrium_coefs(d, &E, &two0);
+    if (!(E > 0.0 && E <= 1.0 / 3.0))
+      return fail(LBW_EINVAL, "equilibrium: the rest population's weight 1 - 3 E must stay in [0, 1) "
+                              "(E = c^2 for moment matching, the Hermite form's stress coefficient otherwise)");
+  }
   if (d.kind == LBW_TRUMPET && d.horn_profile != 0 && d.horn_profile != 1)
     return fail(LBW_EINVAL, "horn_profile must be 0 (Bessel) or 1 (exponential)");
   for (int k = 0; k < 6; ++k)
@@ -156,11 +172,12 @@ lbw_status build_table(const lbw_grid_desc& d, std::vector<double>& tab) {
       const Metric m = metric_at(d, q1, 0, q3);
       if (!m.ok) return fail(LBW_EINVAL, "metric undefined on the lattice (r, s or R + r cos phi <= 0)");
       worst = std::max(worst, c2 * (m.g11 + m.g22 + m.g33) + 3.0 * cs2);
+      e[T_SG] = m.sg;
+      e[T_INVSG] = 1.0 / m.sg;
+      if (d.equilibrium != LBW_EQ_CURVILINEAR) continue;  // the Cartesian schemes have no force
       e[T_H22] = 0.5 * (c2 * m.g22 - cs2);
       e[T_MG1] = -c2 * m.G1;
       e[T_MG3] = -c2 * m.G3;
-      e[T_SG] = m.sg;
-      e[T_INVSG] = 1.0 / m.sg;
       // neighbours along q1 (axis 0) and q3 (axis 2)
       for (int axis = 0; axis < 3; axis += 2)
         for (int s = -1; s <= 1; s += 2) {
@@ -452,7 +469,8 @@ lbw_status lbw_source(lbw_grid* g, const int32_t* host_q, int32_t n, int32_t kin
     h[k].pad = 0;
     h[k].sg = lattice_sqrtg(g->d, q1, q3);
     h[k].omega = omega;
-    h[k].cs2 = g->d.cs2;
+    double eq_two0;
+    equilibrium_coefs(g->d, &h[k].cs2, &eq_two0);  // the equilibrium the source imposes
   }
   drop_graphs(g);  // captured chains carry the source list
   if (g->src) { cudaFreeAsync(g->src, g->stream); g->src = nullptr; }

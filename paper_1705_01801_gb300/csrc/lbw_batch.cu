@@ -897,6 +897,8 @@ lbw_status lbw_batch_create(const lbw_grid_desc* descs, int32_t n, void* stream,
     if (d.prec != b->prec) return cleanup(fail(LBW_EINVAL, "all members must share the storage precision"));
     lbw_status st = validate_desc(d);
     if (st != LBW_OK) return cleanup(fail(st, "member " + std::to_string(m) + ": " + lbw_last_error()));
+    if (d.equilibrium != LBW_EQ_CURVILINEAR)
+      return cleanup(fail(LBW_EINVAL, "member " + std::to_string(m) + ": ensembles run the paper's equilibrium"));
     if (d.geom_mode == LBW_GEOM_ANALYTIC)
       return cleanup(fail(LBW_EINVAL, "member " + std::to_string(m) +
                                           ": ensembles take the geometry from the table (geom_mode ANALYTIC is "

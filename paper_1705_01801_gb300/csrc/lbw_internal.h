@@ -95,6 +95,18 @@ struct SourceEntry {
 // sqrt(g) of lattice node (q1, q3) of desc in lattice coordinates (FP64, as in the table)
 double lattice_sqrtg(const lbw_grid_desc& d, int q1, int q3);
 
+// Collision constants of the equilibrium: 2 f_i^eq = E rho + xi_i . j' (i >= 1, unscaled storage)
+// and 2 f_0^eq = two0 rho.  The paper's method has E = cs^2 (two0 = 2 w0); the Cartesian
+// schemes of Sec. II (lbw_equilibrium) change E and have no forcing term.
+inline void equilibrium_coefs(const lbw_grid_desc& d, double* E, double* two0) {
+  const double cs2 = d.cs2, c2 = d.c * d.c;
+  double e = cs2;
+  if (d.equilibrium == LBW_EQ_MOMENT_MATCHING) e = c2;
+  if (d.equilibrium == LBW_EQ_HERMITE) e = cs2 + (c2 - cs2) * (1.0 - 3.0 * cs2) / (2.0 * cs2);
+  *E = e;
+  *two0 = 2.0 - 6.0 * e;
+}
+
 // population stride of a lattice's storage in elements
 inline long long pop_stride(const Grid* g) {
   return g->pitch ? (long long)g->d.n[0] * g->d.n[2] * g->pitch : g->nn;

@@ -45,7 +45,7 @@ template <> struct Store<__nv_bfloat16> {
 // lattice coordinates (x^a = x0^a + (q^a + 1/2) h^a), evaluated in the arithmetic type R.
 template <typename R>
 struct GeomArgs {
-  int kind, profile, analytic;
+  int kind, profile;
   R x0r, x0w, h0, h1, h2;  // r (or x) and the third coordinate's origin, spacings
   R g0, g1, g2;            // torus R | Bessel horn Zmax, lambda | exponential a0, b, alpha
   R c2, cs2;
@@ -103,13 +103,14 @@ __device__ MetricR<R> metric_q(const GeomArgs<R>& G, int q1, int q3) {
   return m;
 }
 
-// The 16 force coefficients (TableSlot) of row (q1, q3), with the same ghost rules as the
-// host-built table: free -> rho copied; bounce-back -> P mirrored; anti-bounce-back -> P
-// mirrored with opposite sign; periodic neighbours wrap; the ghost's metric at the ghost.
+// The 16 force coefficients (TableSlot) of row (q1, q3) from the metric at the row, m, and at
+// its four neighbours nb = (q1 - 1, q1 + 1, q3 - 1, q3 + 1), each taken at the wrapped position
+// across a periodic face and at the ghost position across any other face.  Ghost rules as in
+// the host-built table: free -> rho copied; bounce-back -> P mirrored; anti-bounce-back -> P
+// mirrored with opposite sign.
 template <typename R>
 __device__ void table_row(const GeomArgs<R>& G, const int (&bc)[6], int n1, int n3, int q1, int q3,
-                          R* out) {
-  const MetricR<R> m = metric_q(G, q1, q3);
+                          const MetricR<R>& m, const MetricR<R> (&nb)[4], R* out) {
   R e[T_SLOTS];
 #pragma unroll
   for (int k = 0; k < T_SLOTS; ++k) e[k] = R(0);
@@ -119,20 +120,12 @@ __device__ void table_row(const GeomArgs<R>& G, const int (&bc)[6], int n1, int 
   e[T_SG] = m.sg;
   e[T_INVSG] = R(1) / m.sg;
 #pragma unroll
-  for (int nb = 0; nb < 4; ++nb) {
-    const int axis = nb < 2 ? 0 : 2, s = (nb & 1) ? 1 : -1;
-    int p1 = q1 + (axis == 0 ? s : 0), p3 = q3 + (axis == 2 ? s : 0);
-    const int n = axis == 0 ? n1 : n3, pos = axis == 0 ? p1 : p3;
+  for (int k = 0; k < 4; ++k) {
+    const int axis = k < 2 ? 0 : 2, s = (k & 1) ? 1 : -1;
+    const int pos = (axis == 0 ? q1 : q3) + s, n = axis == 0 ? n1 : n3;
     const int face = 2 * axis + (s > 0 ? 1 : 0);
-    bool ghost = false;
-    if (pos < 0 || pos >= n) {
-      if (bc[face] == LBW_BC_PERIODIC) {
-        if (axis == 0) p1 = (p1 + n) % n; else p3 = (p3 + n) % n;
-      } else {
-        ghost = true;
-      }
-    }
-    const MetricR<R> mn = metric_q(G, p1, p3);
+    const bool ghost = (pos < 0 || pos >= n) && bc[face] != LBW_BC_PERIODIC;
+    const MetricR<R>& mn = nb[k];
     const R K11 = G.c2 * mn.g11 - G.cs2, K13 = G.c2 * mn.g13, K33 = G.c2 * mn.g33 - G.cs2;
     const R k1 = axis == 0 ? K11 : K13, k3 = axis == 0 ? K13 : K33;
     if (ghost) {

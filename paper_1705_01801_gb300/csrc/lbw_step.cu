@@ -90,7 +90,7 @@ struct TmaLayout {
 // keeps halo rows off the q1 faces and halo columns off the q2 faces.  Shared memory is
 // addressed by 32-bit offsets from the dynamic array.  Every mbarrier wait is bounded: on
 // expiry counters[3] is raised and the CTA stops.
-template <typename S, int BY, int NPT>
+template <typename S, int BY, int NPT, bool ANA>
 __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     const StepArgs<S> a, const __grid_constant__ CUtensorMap tm_main,
     const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_tab) {
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
   // slots, three rho planes, NB coefficient blocks
   const unsigned sbase = smem_u32(smem_raw);
   const unsigned OFF = (128u - (sbase & 127u)) & 127u;
-  const unsigned SL = OFF + 128, RHO = SL + NB * SLOTB, TAB = RHO + RHOB;
+  const unsigned SL = OFF + 128, RHO = SL + NB * SLOTB, TAB = RHO + RHOB, MSC = TAB + NB * TABB;
   auto full_at = [&](int k) { return sbase + OFF + 8u * k; };
   auto empty_at = [&](int k) { return sbase + OFF + 8u * (NB + k); };
   // a barrier that no thread or copy ever completes: the target of the injected timeout
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
 
   if (tid == 0) {
     for (int k = 0; k < NB; ++k) {
-      mbar_init_count(full_at(k), a.geo.analytic ? 2 : 1);  // analytic: the producer's rows arrive too
+      mbar_init_count(full_at(k), ANA ? 2 : 1);  // analytic: the producer's rows arrive too
       mbar_init_count(empty_at(k), NCW);
     }
     mbar_init_count(stall_bar, 1);
@@ -176,10 +176,12 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
   };
 
   if (w == ROWS) {  // ------------------------------------------------------------ producer
-    // Lane 0 issues the copies.  In the analytic geometry mode every lane of the warp waits for
-    // the slot, lanes 0 .. BY - 1 write the coefficient rows of a collided plane into the
-    // slot's table block, and lane 0 adds the slot's second arrival once they are written.
-    const bool ana = a.geo.analytic != 0;
+    // Lane 0 waits for free slots and issues the copies.  In the analytic geometry mode the
+    // other lanes follow it through the loop: after each slot wait they write the coefficient
+    // rows of a collided plane into the slot's table block, and lane 0 adds the slot's second
+    // arrival once they are written.  In the table mode lanes 1 .. 31 stay out of the loop.
+    constexpr bool ana = ANA;
+    if (ana || lane == 0) {
     int xl = x0 - V, xr = x0 + BX;
     const bool hl = xl >= 0 || p2, hr = xr < a.n2 || p2;
     if (xl < 0) xl += a.n2;
@@ -189,8 +191,13 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     int s = 0, use = 0;
     int issued = z0 - 3;
     for (int p = z0 - 2; p <= z1 + (RG ? 0 : 1); ++p) {
-      const bool free_slot = use == 0 || wait_bar(empty_at(s), (unsigned)((use - 1) & 1), kWaitLimit, true);
-      if (!__all_sync(0xffffffffu, free_slot)) break;
+      int free_slot = 1;
+      if (lane == 0 && use > 0) free_slot = wait_bar(empty_at(s), (unsigned)((use - 1) & 1), kWaitLimit, true);
+      if constexpr (ANA) {
+        free_slot = __shfl_sync(0xffffffffu, free_slot, 0);
+        __syncwarp();  // orders lane 0's acquire of the free slot before the others' row writes
+      }
+      if (!free_slot) break;
       const unsigned bar = full_at(s);
       const unsigned base = sbase + SL + s * SLOTB;
       const int pg = resolve(p, a.n3, p3);
@@ -247,14 +254,23 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
           if (tab && !ana) tma_load_3d(sbase + TAB + s * TABB, &tm_tab, 0, y0, pg, bar);
         }
       }
-      if (ana) {
-        if (tab && lane < BY) {
-          R* rowp = reinterpret_cast<R*>(smem_raw + TAB + s * TABB) + lane * T_SLOTS;
-          if (y0 + lane < a.n1) {
-            table_row(a.geo, a.bc, a.n1, a.n3, y0 + lane, pg, rowp);
-          } else {
-#pragma unroll
-            for (int k = 0; k < T_SLOTS; ++k) rowp[k] = R(0);
+      if constexpr (ANA) {
+        if (tab) {
+          // the metric at rows y0 - 1 .. y0 + BY of planes pg - 1, pg, pg + 1, one position per
+          // lane (wrapped across a periodic q3 face, at the ghost position across any other),
+          // then lanes 0 .. BY - 1 assemble the tile's rows from it
+          MetricR<R>* msc = reinterpret_cast<MetricR<R>*>(smem_raw + MSC);
+          for (int k = lane; k < 3 * ROWS; k += 32) {
+            int q3n = pg + k / ROWS - 1;
+            if (p3) q3n = q3n < 0 ? q3n + a.n3 : (q3n >= a.n3 ? q3n - a.n3 : q3n);
+            msc[k] = metric_q(a.geo, y0 - 1 + k % ROWS, q3n);
+          }
+          __syncwarp();
+          if (lane < BY) {
+            R* rowp = reinterpret_cast<R*>(smem_raw + TAB + s * TABB) + lane * T_SLOTS;
+            const MetricR<R> nb[4] = {msc[ROWS + lane], msc[ROWS + lane + 2], msc[lane + 1],
+                                      msc[2 * ROWS + lane + 1]};
+            table_row(a.geo, a.bc, a.n1, a.n3, y0 + lane, pg, msc[ROWS + lane + 1], nb, rowp);
           }
         }
         __syncwarp();
@@ -269,6 +285,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
         const int k = p - (z0 - 2);
         wait_bar(full_at(k % NB), (unsigned)((k / NB) & 1));
       }
+    }
   } else {  // ------------------------------------------------------------------- consumers
     const int q1 = y0 - 1 + w;
     const bool interior = w >= 1 && w <= BY;
@@ -651,8 +668,10 @@ StepArgs<S> make_args(Grid* g, int src) {
   a.nn = g->nn;
   for (int k = 0; k < 6; ++k) a.bc[k] = g->d.bc[k];
   a.damping = (R)g->d.damping;
-  a.cs2 = (R)g->d.cs2;
-  a.two_w0 = (R)(2.0 * g->w0);
+  double eq_e, eq_two0;
+  equilibrium_coefs(g->d, &eq_e, &eq_two0);
+  a.cs2 = (R)eq_e;  // cs^2 for the paper's method; the Cartesian equilibria change it
+  a.two_w0 = (R)eq_two0;
   for (int i = 0; i < 7; ++i) {
     double w = i == 0 ? g->w0 : g->w1;
     a.w[i] = (R)w;
@@ -671,7 +690,6 @@ StepArgs<S> make_args(Grid* g, int src) {
   a.ps = pop_stride(g);
   a.geo.kind = g->d.kind;
   a.geo.profile = g->d.horn_profile;
-  a.geo.analytic = g->d.geom_mode == LBW_GEOM_ANALYTIC && g->tma_by > 0;
   a.geo.x0r = (R)g->d.x0[0];
   a.geo.x0w = (R)g->d.x0[2];
   a.geo.h0 = (R)g->d.h[0];
@@ -685,27 +703,34 @@ StepArgs<S> make_args(Grid* g, int src) {
   return a;
 }
 
-template <typename S, int BY, int NPT>
+template <typename S, int BY, int NPT, bool ANA>
 constexpr size_t tma_smem_bytes() {
   using R = typename Store<S>::R;
   constexpr int BX = 32 * NPT, NB = 5, PS = (BY + 2) * (BX + 2 * NPT);
   constexpr int TABB = ((BY * T_SLOTS * (int)sizeof(R)) + 127) / 128 * 128;
   return 128 /* alignment slack */ + 128 /* barriers */ +
          (size_t)NB * TmaLayout<BY, BX>::template slot_bytes<S>() +
-         ((3 * PS * sizeof(R) + 127) / 128) * 128 + (size_t)NB * TABB;  // see step_tma_kernel
+         ((3 * PS * sizeof(R) + 127) / 128) * 128 + (size_t)NB * TABB +
+         (ANA ? ((3 * (BY + 2) * sizeof(MetricR<R>) + 127) / 128) * 128 : 0);  // see step_tma_kernel
 }
 
-// The tile kernel for (rows BY, nodes per lane NPT): f(kernel, dynamic shared bytes).  Four
-// nodes per lane (128-column tiles) exist for the 16-bit storage formats only.
+// The tile kernel for (rows BY, nodes per lane NPT, analytic geometry or not): f(kernel,
+// dynamic shared bytes).  Four nodes per lane (128-column tiles) exist for the 16-bit storage
+// formats only, the analytic geometry for 32- and 64-bit storage only; the table-geometry
+// kernels carry none of the analytic code.
 template <typename S, typename F>
-auto tma_dispatch(int by, int npt, F&& f) {
+auto tma_dispatch(int by, int npt, bool ana, F&& f) {
   if constexpr (sizeof(S) == 2) {
     if (npt == 4)
-      return by == 7 ? f(step_tma_kernel<S, 7, 4>, tma_smem_bytes<S, 7, 4>())
-                     : f(step_tma_kernel<S, 4, 4>, tma_smem_bytes<S, 4, 4>());
+      return by == 7 ? f(step_tma_kernel<S, 7, 4, false>, tma_smem_bytes<S, 7, 4, false>())
+                     : f(step_tma_kernel<S, 4, 4, false>, tma_smem_bytes<S, 4, 4, false>());
+  } else {
+    if (ana)
+      return by == 7 ? f(step_tma_kernel<S, 7, 2, true>, tma_smem_bytes<S, 7, 2, true>())
+                     : f(step_tma_kernel<S, 4, 2, true>, tma_smem_bytes<S, 4, 2, true>());
   }
-  return by == 7 ? f(step_tma_kernel<S, 7, 2>, tma_smem_bytes<S, 7, 2>())
-                 : f(step_tma_kernel<S, 4, 2>, tma_smem_bytes<S, 4, 2>());
+  return by == 7 ? f(step_tma_kernel<S, 7, 2, false>, tma_smem_bytes<S, 7, 2, false>())
+                 : f(step_tma_kernel<S, 4, 2, false>, tma_smem_bytes<S, 4, 2, false>());
 }
 
 template <typename S>
@@ -724,7 +749,7 @@ cudaError_t launch_step_t(Grid* g, int src) {
     cfg.stream = g->stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return tma_dispatch<S>(g->tma_by, g->tma_npt, [&](auto kern, size_t smem) {
+    return tma_dispatch<S>(g->tma_by, g->tma_npt, g->d.geom_mode == LBW_GEOM_ANALYTIC, [&](auto kern, size_t smem) {
       cfg.dynamicSmemBytes = smem;
       return cudaLaunchKernelEx(&cfg, kern, a, m[2 * src], m[2 * src + 1], m[4]);
     });
@@ -741,8 +766,8 @@ struct TmaInfo {
 };
 
 template <typename S>
-TmaInfo tma_info_t(int by, int npt) {
-  return tma_dispatch<S>(by, npt, [&](auto kern, size_t smem) {
+TmaInfo tma_info_t(int by, int npt, bool ana) {
+  return tma_dispatch<S>(by, npt, ana, [&](auto kern, size_t smem) {
     cudaFuncAttributes at;
     int regs = 255;
     if (cudaFuncGetAttributes(&at, kern) == cudaSuccess) regs = at.numRegs;
@@ -752,18 +777,18 @@ TmaInfo tma_info_t(int by, int npt) {
 }
 
 template <typename S>
-cudaError_t tma_prepare_t(int by, int npt) {
-  return tma_dispatch<S>(by, npt, [&](auto kern, size_t smem) {
+cudaError_t tma_prepare_t(int by, int npt, bool ana) {
+  return tma_dispatch<S>(by, npt, ana, [&](auto kern, size_t smem) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
 }
 
-TmaInfo tma_info(int prec, int by, int npt) {
+TmaInfo tma_info(int prec, int by, int npt, bool ana) {
   switch (prec) {
-    case LBW_F64: return tma_info_t<double>(by, npt);
-    case LBW_F32: return tma_info_t<float>(by, npt);
-    case LBW_F16S: return tma_info_t<__half>(by, npt);
-    default: return tma_info_t<__nv_bfloat16>(by, npt);
+    case LBW_F64: return tma_info_t<double>(by, npt, ana);
+    case LBW_F32: return tma_info_t<float>(by, npt, ana);
+    case LBW_F16S: return tma_info_t<__half>(by, npt, ana);
+    default: return tma_info_t<__nv_bfloat16>(by, npt, ana);
   }
 }
 
@@ -1147,12 +1172,13 @@ void step_launch_shape(Grid* g) {
   }
   g->tma_by = 0;
   const int npt = (g->elem == 2 && n2 % 128 == 0) ? 4 : 2, bx = 32 * npt;
+  const bool ana = g->d.geom_mode == LBW_GEOM_ANALYTIC;
   if (n2 % bx == 0 && g->d.bc[0] != LBW_BC_PERIODIC && g->nn * 7 < (1LL << 31)) {
     const int bys[2] = {4, 7};
     int per_sm_of[2] = {0, 0};
     for (int c = 0; c < 2; ++c) {
       const int by = bys[c], threads = 32 * (by + 3);
-      const TmaInfo ti = tma_info(g->d.prec, by, npt);
+      const TmaInfo ti = tma_info(g->d.prec, by, npt, ana);
       if ((long long)ti.smem > smem_max || ti.regs > 255) continue;
       if ((n1 - 1) % by == 0) continue;  // a halo row would sit on the q1 = n1 - 1 face
       const int rr = (ti.regs + 7) & ~7;
@@ -1182,7 +1208,7 @@ void step_launch_shape(Grid* g) {
     }
     if (g->tma_by > 0) {
       g->tma_npt = npt;
-      cudaError_t e = dispatch(g->d.prec, [&](auto tag) { return tma_prepare_t<decltype(tag)>(g->tma_by, npt); });
+      cudaError_t e = dispatch(g->d.prec, [&](auto tag) { return tma_prepare_t<decltype(tag)>(g->tma_by, npt, ana); });
       if (e == cudaSuccess && build_tmaps(g, g->tma_by, bx)) {
         g->grid_dim = dim3(n2 / bx, (n1 + g->tma_by - 1) / g->tma_by, (n3 + g->lz - 1) / g->lz);
         return;

@@ -36,7 +36,8 @@ class lbw_grid_desc(ctypes.Structure):
                 ("cs2", ctypes.c_double), ("damping", ctypes.c_double),
                 ("geom", ctypes.c_double * 4), ("horn_profile", ctypes.c_int32),
                 ("bc", ctypes.c_int32 * 6), ("prec", ctypes.c_int32),
-                ("geom_mode", ctypes.c_int32)]
+                ("geom_mode", ctypes.c_int32), ("equilibrium", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class lbw_pulse(ctypes.Structure):
@@ -154,6 +155,8 @@ def make_desc(spec) -> lbw_grid_desc:
         d.bc[k] = int(spec.bc[k])
     d.prec = spec.prec
     d.geom_mode = int(getattr(spec, "geom_mode", 0))
+    d.equilibrium = int(getattr(spec, "equilibrium", 0))
+    d.reserved = 0
     return d
 
 

@@ -84,3 +84,53 @@ class Surrogate:
         Xn = ((np.asarray(X, np.float64) - self.mx) / self.sx).astype(np.float32)
         Yn = self.net.predict_bf16(Xn) if bf16 else self.net.forward(Xn)
         return np.exp(Yn.astype(np.float64) * self.sy + self.my)
+
+
+class SurrogateEnsemble:
+    """k independently initialised surrogates answering together.  The answer is their mean in
+    log-frequency; the spread between them (largest standard deviation of log f over the
+    modes) measures how far a query lies from what the training data pins down.  Queries whose
+    spread exceeds a calibrated threshold fall back to the lattice-Boltzmann ensemble, which
+    stays the judge of the error: a fallback answer is the LBM's own."""
+
+    def __init__(self, k: int = 4, **kw):
+        self.members = [Surrogate(seed=s, **kw) for s in range(k)]
+        self.threshold = np.inf
+
+    def fit(self, X, Y, **kw):
+        return [m.fit(X, Y, seed=i, **kw) for i, m in enumerate(self.members)]
+
+    def predict(self, X, bf16: bool = True):
+        """(mean frequencies [n, modes], spread [n])."""
+        logp = np.log(np.stack([m.predict(X, bf16) for m in self.members]))
+        return np.exp(logp.mean(0)), logp.std(0).max(1)
+
+    def calibrate(self, X, Y, target: float):
+        """Largest spread threshold at which the accepted queries of (X, Y) keep a mean relative
+        error <= target; returns the fraction accepted."""
+        pred, spread = self.predict(X)
+        err = (np.abs(pred - Y) / Y).mean(1)
+        order = np.argsort(spread)
+        mean_err = np.cumsum(err[order]) / np.arange(1, len(err) + 1)
+        ok = np.nonzero(mean_err <= target)[0]
+        if len(ok) == 0:
+            self.threshold = -np.inf
+            return 0.0
+        last = ok[-1]
+        self.threshold = spread[order[last]]
+        return (last + 1) / len(err)
+
+    def answer(self, specs, X, steps: int, n_modes: int = 8):
+        """Frequencies for every query: the ensemble's mean where its spread is within the
+        threshold, the LBM's measurement (``measure``) elsewhere.  Returns (freqs, fell_back
+        mask, seconds of surrogate work, seconds of LBM work)."""
+        t0 = time.perf_counter()
+        pred, spread = self.predict(X)
+        sur_s = time.perf_counter() - t0
+        back = spread > self.threshold
+        lbm_s = 0.0
+        if back.any():
+            sub = [s for s, b in zip(specs, back) if b]
+            f, valid, lbm_s = measure(sub, steps=steps, n_modes=n_modes, tune=False)
+            pred[back] = np.where(valid[:, None], f, np.nan)
+        return pred, back, sur_s, lbm_s

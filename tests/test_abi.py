@@ -31,7 +31,8 @@ def test_struct_layout_matches_header():
     # kind(4) n(12) pad(0) h(24)...: offsets follow C rules for the declared field order
     d = lbw.lbw_grid_desc
     assert d.h.offset == 16 and d.c.offset == 64 and d.geom.offset == 96
-    assert ctypes.sizeof(d) == 168
+    assert d.geom_mode.offset == 160 and d.equilibrium.offset == 164 and d.reserved.offset == 168
+    assert ctypes.sizeof(d) == 176
     assert ctypes.sizeof(lbw.lbw_pulse) == 40
 
 
@@ -74,8 +75,11 @@ def _desc(**kw):
     ({"c": 1.5}, "too coarse"),                      # beyond the stability bound
     ({"x0": (-6.0, 0.0, 0.0)}, "metric undefined"),  # r <= 0 on the lattice
     ({"geom_mode": 3}, "geom_mode"),
+    ({"equilibrium": 3}, "equilibrium"),
+    ({"equilibrium": 1}, "Cartesian"),                # moment matching on a cylinder
+    ({"reserved": 2}, "reserved"),
 ], ids=["kind", "damping", "prec", "periodic-pair", "angular", "horn", "stability", "metric",
-        "geom-mode"])
+        "geom-mode", "equilibrium", "eq-kind", "reserved"])
 def test_descriptor_rules_are_checked_on_the_host(fields, message):
     """Every descriptor rule of lbw_create_grid is decided before any CUDA call: the status is
     LBW_EINVAL and the thread's last error names the rule."""
