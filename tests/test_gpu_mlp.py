@@ -91,38 +91,42 @@ def test_surrogate_against_ensemble():
 
 
 def test_surrogate_ensemble_with_lbm_fallback():
-    """Four independently initialised networks answer together; their spread flags the
-    geometries the training data does not pin down, and those fall back to the batched LBM,
-    which stays the judge: a fallback answer is the LBM's own measurement, bit for bit.  The
-    spread threshold is calibrated on a validation split for a mean relative error of 0.5 %;
-    on the held-out split the delivered answers (network where accepted, LBM elsewhere) keep
-    the mean error near that target, and the test reports the fallback rate and the speedup
-    that remains over running the LBM for every geometry."""
+    """The surrogate at the 0.5 % mode-frequency target, with the LBM as fallback and judge.
+
+    4096 seeded small trumpets run 8000 steps in one ensemble; their two lowest mode
+    frequencies are the targets (the lowest modes the excitation and probes resolve in every
+    member; higher ones reach 1-3 % held-out error at this data size).  Four independently
+    initialised networks answer together and their spread flags geometries the training data
+    does not pin down; those fall back to the batched LBM, whose answer is its own measurement,
+    bit for bit.  The spread threshold is calibrated on a validation split for a mean relative
+    error of 0.5 %, then the held-out split is answered: the delivered answers (networks where
+    accepted, LBM elsewhere) must meet the target, most of them from the networks."""
     import lbw_workloads as W
     from paper_1705_01801_gb300 import surrogate as S
-    specs, _ = W.ensemble(384, seed=21, r_range=(12, 24), theta_range=(32, 48), z_range=(40, 80))
-    freqs, valid, lbm_s = S.measure(specs, steps=4000, tune=False)
+    specs, _ = W.ensemble(4096, seed=21, r_range=(12, 24), theta_range=(32, 48), z_range=(40, 80))
+    freqs, valid, lbm_s = S.measure(specs, steps=8000, n_modes=2, tune=False)
     keep = np.nonzero(valid)[0]
     X = np.stack([S.features(specs[i]) for i in keep])
     Y = freqs[keep]
-    n = len(keep)
-    ntr, nval = int(0.6 * n), int(0.2 * n)
-    ens = S.SurrogateEnsemble(k=4, hidden=256, depth=4)
-    ens.fit(X[:ntr], Y[:ntr], steps=3000, batch=32, lr=1e-3)
+    n, nval, ntest = len(keep), 400, 400
+    ntr = n - nval - ntest
+    ens = S.SurrogateEnsemble(k=4, out_dim=2, hidden=256, depth=4)
+    ens.fit(X[:ntr], Y[:ntr], steps=4000, batch=32, lr=1e-3)
     accepted_val = ens.calibrate(X[ntr:ntr + nval], Y[ntr:ntr + nval], target=0.005)
     test = slice(ntr + nval, n)
     test_specs = [specs[i] for i in keep[test]]
-    pred, back, sur_s, fb_s = ens.answer(test_specs, X[test], steps=4000)
+    net_only, _ = ens.predict(X[test])
+    net_err = (np.abs(net_only - Y[test]) / Y[test]).mean(1)
+    one_err = (np.abs(ens.members[0].predict(X[test]) - Y[test]) / Y[test]).mean(1)
+    pred, back, sur_s, fb_s = ens.answer(test_specs, X[test], steps=8000, n_modes=2)
     err = (np.abs(pred - Y[test]) / Y[test]).mean(1)
-    single, _ = ens.predict(X[test])
-    single_err = (np.abs(ens.members[0].predict(X[test]) - Y[test]) / Y[test]).mean(1)
     lbm_per = lbm_s / len(specs)
-    per_query = (sur_s + fb_s) / len(test_specs)
-    print(f"\nheld-out {len(test_specs)}: one network {single_err.mean():.4f}, ensemble "
-          f"{(np.abs(single - Y[test]) / Y[test]).mean():.4f}; accepted on validation "
-          f"{accepted_val:.2f}, fallback rate {back.mean():.2f}, delivered mean error "
-          f"{err.mean():.4f} (accepted {err[~back].mean() if (~back).any() else float('nan'):.4f}); "
-          f"{lbm_per * 1e3:.1f} ms per geometry by the LBM, {per_query * 1e3:.2f} ms per answer")
+    per_answer = (sur_s + fb_s) / len(test_specs)
+    print(f"\n{ntr} training geometries, held-out {len(test_specs)}: one network {one_err.mean():.4f}, "
+          f"four {net_err.mean():.4f} (per mode {np.round((np.abs(net_only - Y[test]) / Y[test]).mean(0), 4)}); "
+          f"accepted on validation {accepted_val:.2f}, fallback rate {back.mean():.2f}, delivered mean error "
+          f"{err.mean():.4f}; {lbm_per * 1e3:.2f} ms per geometry by the LBM, {per_answer * 1e3:.2f} ms per answer")
     assert np.all(err[back] == 0.0)  # a fallback answer is the LBM's own
-    assert err.mean() <= 0.0075
-    assert back.mean() < 1.0
+    assert net_err.mean() < 0.01 and net_err.mean() <= one_err.mean()
+    assert err.mean() <= 0.006
+    assert back.mean() < 0.5
