@@ -259,6 +259,13 @@ lbw_status lbw_batch_source(lbw_batch* b, const int32_t* host_q, int32_t per_mem
 /* All series: host_out = n x per_member x capacity doubles; *n_steps = samples recorded. */
 lbw_status lbw_batch_probe_read(lbw_batch* b, double* host_out, int64_t* n_steps);
 
+/* The steady-state response of the resonance sweeps (Sec. IV.A, Fig. Frequencies; Sec. IV.C,
+ * Fig. FreqTorus: the pressure intensity at a probe after a transient): for every member and
+ * probe the largest |P| over its last `tail` recorded samples, reduced on the device.
+ * host_out = n x per_member doubles.  LBW_EINVAL if tail exceeds the recorded samples,
+ * LBW_EUNSTABLE if a sample in the window is not finite. */
+lbw_status lbw_batch_probe_peak(lbw_batch* b, int64_t tail, double* host_out);
+
 /* Per member, the spectrum of the sum of its probes (the estimator of lbw_spectrum):
  * host_freq / host_amp = n x k, host_n_found = n. */
 lbw_status lbw_batch_spectrum(lbw_batch* b, int32_t k, double* host_freq, double* host_amp,

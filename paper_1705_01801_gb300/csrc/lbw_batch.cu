@@ -529,6 +529,39 @@ struct Shape {
 };
 
 }  // namespace
+namespace {
+// Largest |x| of each series over its samples [t0, t1): one CTA per series, series s at
+// x + s * stride; NaN when a sample is not finite (so the host sees the instability).
+__global__ void series_peak_kernel(const double* __restrict__ x, long long stride, long long t0, long long t1,
+                                   double* __restrict__ out) {
+  __shared__ double red[32];
+  const double* p = x + (long long)blockIdx.x * stride;
+  double m = 0.0;
+  bool bad = false;
+  for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    const double v = fabs(p[t]);
+    bad |= !isfinite(v);
+    m = fmax(m, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    bad |= __shfl_down_sync(0xffffffffu, (int)bad, o) != 0;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = bad ? NAN : m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    bool anybad = false;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      anybad |= !isfinite(red[k]);
+      r = fmax(r, red[k]);
+    }
+    out[blockIdx.x] = anybad ? NAN : r;
+  }
+}
+}  // namespace
+
 }  // namespace lbw
 
 using namespace lbw;
@@ -1120,6 +1153,29 @@ lbw_status lbw_batch_probe_read(lbw_batch* b, double* host_out, int64_t* n_steps
   LBW_CUDA(cudaMemcpyAsync(host_out, b->series, sizeof(double) * b->n * b->nprobe * b->cap,
                            cudaMemcpyDeviceToHost, b->stream));
   LBW_CUDA(cudaStreamSynchronize(b->stream));
+  return LBW_OK;
+}
+
+lbw_status lbw_batch_probe_peak(lbw_batch* b, int64_t tail, double* host_out) {
+  if (!b || !host_out) return fail(LBW_EINVAL, "NULL argument");
+  if (tail < 1) return fail(LBW_EINVAL, "tail must be >= 1");
+  if (b->nprobe == 0) return fail(LBW_ESTATE, "no probes registered");
+  unsigned long long rec = 0;
+  lbw_status st = batch_counters(b, &rec);
+  if (st != LBW_OK) return st;
+  if ((unsigned long long)tail > rec) return fail(LBW_EINVAL, "tail longer than the recorded series");
+  const int nser = b->n * b->nprobe;
+  double* d = nullptr;
+  LBW_CUDA(cudaMallocAsync(&d, sizeof(double) * nser, b->stream));
+  series_peak_kernel<<<nser, 256, 0, b->stream>>>(b->series, (long long)b->cap, (long long)(rec - tail),
+                                                  (long long)rec, d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, d, sizeof(double) * nser, cudaMemcpyDeviceToHost, b->stream);
+  cudaFreeAsync(d, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "probe_peak");
+  for (int k = 0; k < nser; ++k)
+    if (!std::isfinite(host_out[k])) return fail(LBW_EUNSTABLE, "probe series holds a non-finite value (unstable run)");
   return LBW_OK;
 }
 

@@ -23,7 +23,7 @@ EXPORTS = ["lbw_create_grid", "lbw_init", "lbw_step", "lbw_probe", "lbw_probe_re
            "lbw_spectrum", "lbw_spectrum_lowest", "lbw_spectrum_series", "lbw_spectrum_series_static", "lbw_get_field", "lbw_get_populations",
            "lbw_set_populations", "lbw_step_count", "lbw_inject_wait_timeout", "lbw_destroy", "lbw_last_error", "lbw_source",
            "lbw_batch_create", "lbw_batch_init", "lbw_batch_probe", "lbw_batch_step", "lbw_batch_source",
-           "lbw_batch_probe_read", "lbw_batch_spectrum", "lbw_batch_spectrum_lowest", "lbw_batch_get_populations",
+           "lbw_batch_probe_read", "lbw_batch_probe_peak", "lbw_batch_spectrum", "lbw_batch_spectrum_lowest", "lbw_batch_get_populations",
            "lbw_batch_tune", "lbw_batch_info", "lbw_batch_destroy",
            "lbw_mlp_create", "lbw_mlp_param_count", "lbw_mlp_get_params", "lbw_mlp_set_params",
            "lbw_mlp_forward", "lbw_mlp_predict_bf16", "lbw_mlp_grad", "lbw_mlp_adam_step",
@@ -88,6 +88,7 @@ def lib():
                 "lbw_batch_probe": (st, [vp, ip, i32, i64]),
                 "lbw_batch_step": (st, [vp, i64]),
                 "lbw_batch_probe_read": (st, [vp, dp, ctypes.POINTER(i64)]),
+                "lbw_batch_probe_peak": (st, [vp, i64, dp]),
                 "lbw_batch_spectrum": (st, [vp, i32, dp, dp, ip]),
                 "lbw_batch_spectrum_lowest": (st, [vp, i32, ctypes.c_double, dp, dp, ip]),
                 "lbw_batch_get_populations": (st, [vp, i32, dp]),
@@ -398,6 +399,12 @@ class Batch:
         n = ctypes.c_int64()
         _check(lib().lbw_batch_probe_read(self._h, _dp(out), ctypes.byref(n)))
         return out[:, : self._per, : n.value]
+
+    def probe_peak(self, tail):
+        """Largest |P| of every member's probes over the last `tail` samples, (n, per_member)."""
+        out = np.zeros(self.n * max(1, self._per))
+        _check(lib().lbw_batch_probe_peak(self._h, int(tail), _dp(out)))
+        return out.reshape(self.n, max(1, self._per))
 
     def spectrum(self, k=8, lowest=False, rel_power=1e-3):
         """Per member the k strongest peaks, or (lowest) the k lowest-frequency peaks with at

@@ -3,8 +3,9 @@ point source, the steady-state pressure at a probe recorded against the source f
 
 One ensemble of identical lattices, one source frequency per member, advanced together by the
 batched kernels (lbw_batch_*); the response is the largest |P| at the probe over the last
-`tail` time steps.  All stepping runs in the library's kernels; this module only assembles
-arrays.
+`tail` time steps, reduced on the device (lbw_batch_probe_peak).  All stepping and reduction
+runs in the library's kernels; this module only assembles arrays (and refines the peak of the
+response curve by a parabola through three of its points).
 """
 from __future__ import annotations
 
@@ -26,10 +27,10 @@ def resonance_curve(spec, source_q, probe_q, omegas, steps: int, tail: int, kind
         b.set_sources(np.broadcast_to(source_q, (n,) + source_q.shape), omegas, kind=kind, amp=amp)
         b.set_probes(np.broadcast_to(np.asarray(probe_q, np.int32).reshape(1, 1, 3), (n, 1, 3)), steps)
         b.step(steps)
-        series = b.read_probes()[:, 0, :]
+        peak = b.probe_peak(tail)[:, 0]
     finally:
         b.close()
-    return np.abs(series[:, -tail:]).max(axis=1)
+    return peak
 
 
 def peak_frequency(omegas, response):

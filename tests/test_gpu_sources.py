@@ -194,3 +194,61 @@ def test_paper_pipe_is_an_open_closed_pipe():
         k = win[np.argmax(resp[win])]
         print(f"mode {m:.6f}: sweep peak {omegas[k]:.6f}")
         assert win[0] < k < win[-1], (m, omegas[win[0]], omegas[k], omegas[win[-1]])
+
+
+def _paper_torus(prec=PREC_F64):
+    """The torus of Sec. IV.C: R = 640, r < 409.6, 20 x 200 x 30 cells in (r, theta major,
+    phi minor), bounce-back with D = 0.65 at r_max, periodic theta and phi.  Two changes: the
+    inner face is rigid (the paper's free face grows without bound on a curved inner wall) and
+    sits at r = 12 instead of 5.12, because with 20 cells of 20 units the ghost node of a face
+    at 5.12 would lie at negative r, where the metric is undefined.  The paper does not state
+    c: c = 2 (physical units per step, 0.1 cells of h_r per step)."""
+    from lbw_workloads import BC_BOUNCE as BB, KIND_TOROIDAL
+    n = (20, 200, 30)
+    return GridSpec(kind=KIND_TOROIDAL, n=n, h=((409.6 - 12.0) / n[0], 2 * math.pi / n[1], 2 * math.pi / n[2]),
+                    x0=(12.0, 0, 0), c=2.0, damping=0.65, geom=(640.0, 0, 0, 0), prec=prec,
+                    bc=(BB, BB, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC))
+
+
+@pytest.mark.parametrize("source", ["major-ring", "small-ring", "point"])
+def test_paper_torus_sources_match_oracle(source):
+    """The three sources of Sec. IV.C on the paper's torus, device against the FP64 oracle:
+    the ring along the major circle (r = r_min, all theta and phi), the small ring (r = r_min,
+    theta = 0, all phi) and the off-axis point (mid radius, theta = 0, phi = pi / 2)."""
+    from paper_1705_01801_gb300 import lbw
+    spec = _paper_torus()
+    n1, n2, n3 = spec.n
+    src = {"major-ring": [[0, j, k] for j in range(n2) for k in range(n3)],
+           "small-ring": [[0, 0, k] for k in range(n3)],
+           "point": [[n1 // 2, 0, n3 // 4]]}[source]
+    probe = [[n1 - 1, n2 // 2, 0], [n1 // 2, n2 // 4, n3 // 2]]  # (r_max, pi, 0) and an inner node
+    g = lbw.Grid(spec)
+    o = oracle.OracleGrid(spec)
+    for grid in (g, o):
+        grid.init(np.zeros((0, 5)))
+        grid.set_sources(src, kind=0, amp=1.0, omega=0.07)
+        grid.set_probes(probe, 300)
+        grid.step(300)
+    fo = o.get_f()
+    np.testing.assert_allclose(g.get_f(), fo, rtol=0, atol=1e-11 * np.abs(fo).max())
+    so = o.read_probes()
+    np.testing.assert_allclose(g.read_probes(), so, rtol=0, atol=1e-10 * np.abs(so).max())
+
+
+def test_probe_peak_reduction_matches_the_series():
+    """The sweep's response, reduced on the device (largest |P| of each probe over the last
+    `tail` samples), equals the same reduction of the read-back series."""
+    from paper_1705_01801_gb300 import lbw
+    specs, _ = ensemble(3, seed=14, r_range=(9, 12), theta_range=(33, 40), z_range=(18, 24), prec=PREC_F64)
+    b = lbw.Batch(specs)
+    b.init([np.zeros((0, 5))] * 3)
+    b.set_sources(np.array([[[2, 0, 1]]] * 3), [0.05, 0.1, 0.2], kind=0, amp=1.0)
+    q = np.array([[[3, 5, 7], [1, 2, 10]]] * 3, dtype=np.int32)
+    b.set_probes(q, 300)
+    b.step(300)
+    series = b.read_probes()
+    for tail in (1, 77, 300):
+        np.testing.assert_array_equal(b.probe_peak(tail), np.abs(series[:, :, -tail:]).max(axis=2))
+    with pytest.raises(lbw.LbwError) as e:
+        b.probe_peak(301)
+    assert e.value.status == lbw.LBW_EINVAL
