@@ -923,20 +923,28 @@ struct InitGeom {
 };
 
 __device__ void embed_dev(const InitGeom& G, double u1, double u2, double u3, double X[3]) {
+  double s2, c2;
   switch (G.kind) {
     case LBW_CARTESIAN: X[0] = u1; X[1] = u2; X[2] = u3; break;
     case LBW_POLAR:
-    case LBW_CYLINDRICAL: X[0] = u1 * cos(u2); X[1] = u1 * sin(u2); X[2] = u3; break;
+    case LBW_CYLINDRICAL:
+      sincos(u2, &s2, &c2);
+      X[0] = u1 * c2; X[1] = u1 * s2; X[2] = u3;
+      break;
     case LBW_TRUMPET: {
       double s;
       if (G.profile == 0) s = pow(G.geom[0] - u3, -G.geom[1]);
       else s = (G.geom[0] + G.geom[1] * exp(G.geom[2] * u3)) / (G.geom[0] + G.geom[1]);
-      X[0] = u1 * s * cos(u2); X[1] = u1 * s * sin(u2); X[2] = u3;
+      sincos(u2, &s2, &c2);
+      X[0] = u1 * s * c2; X[1] = u1 * s * s2; X[2] = u3;
       break;
     }
     default: {
-      double rr = G.geom[0] + u1 * cos(u3);
-      X[0] = rr * cos(u2); X[1] = rr * sin(u2); X[2] = u1 * sin(u3);
+      double s3, c3;
+      sincos(u3, &s3, &c3);
+      sincos(u2, &s2, &c2);
+      const double rr = G.geom[0] + u1 * c3;
+      X[0] = rr * c2; X[1] = rr * s2; X[2] = u1 * s3;
     }
   }
 }
@@ -959,7 +967,8 @@ __global__ void init_rho_kernel(InitGeom G, const double* __restrict__ pulses, i
       const double* p = pulses + 5 * k;
       const double d2 = (X[0] - p[0]) * (X[0] - p[0]) + (X[1] - p[1]) * (X[1] - p[1]) +
                         (X[2] - p[2]) * (X[2] - p[2]);
-      P0 += p[4] * exp(-d2 / (2.0 * p[3] * p[3]));
+      const double e = d2 / (2.0 * p[3] * p[3]);
+      if (e < 80.0) P0 += p[4] * exp(-e);  // beyond: below 2e-35 of the amplitude
     }
     rho0[x] = (R)((double)tab[((long long)q3 * n1 + q1) * T_SLOTS + T_SG] * P0);
   }
