@@ -94,7 +94,8 @@ typedef struct {
  * c^2 P delta for any c; HERMITE is the truncated Hermite equilibrium of Eq. EquilibriumHermite,
  * f_i = w_i [P + xi_i . J / cs^2 + P (c^2 - cs^2)(|xi_i|^2 - 3 cs^2) / (2 cs^4)], f_0 = P - sum
  * of the others, whose wave speed on D3Q7 is c only at cs^2 = 1/5 (in general c_eff^2 =
- * cs^2 + (c^2 - cs^2)(1 - 3 cs^2) / (2 cs^2)).  Neither uses a forcing term. */
+ * cs^2 + (c^2 - cs^2)(1 - 3 cs^2) / (2 cs^2)).  Neither uses a forcing term; both take c in
+ * cells per step (h is not applied) and need the rest weight 1 - 3 E >= 0, E = c^2 or c_eff^2. */
 typedef enum { LBW_EQ_CURVILINEAR = 0, LBW_EQ_MOMENT_MATCHING = 1, LBW_EQ_HERMITE = 2 } lbw_equilibrium;
 
 /* Geometry source of the fused step (Sec. IV: sqrt g, g^{ab} and G^a enter every node's
@@ -102,9 +103,9 @@ typedef enum { LBW_EQ_CURVILINEAR = 0, LBW_EQ_MOMENT_MATCHING = 1, LBW_EQ_HERMIT
  * TABLE: built once on the host in FP64, rounded to the arithmetic type, staged per plane by
  * TMA with the populations.  ANALYTIC: recomputed per row and plane inside the step kernel
  * from the closed-form metric in the arithmetic type (FP32 or FP64), by the producer warp's
- * lanes; only lattices on the tile kernel (q2 extent a multiple of the tile width,
- * non-periodic q1) and single lattices (not ensembles) accept it.  AUTO takes the table, the
- * faster of the two on the benchmark lattices (measured). */
+ * lanes; only single lattices (not ensembles) with FP32 or FP64 storage on the tile kernel
+ * (q2 extent a multiple of 64, non-periodic q1) accept it.  AUTO takes the table, the faster of
+ * the two on the benchmark lattices (measured: 472 against 966 us per torus step). */
 typedef enum { LBW_GEOM_AUTO = 0, LBW_GEOM_TABLE = 1, LBW_GEOM_ANALYTIC = 2 } lbw_geom_mode;
 
 /* A Gaussian pulse P0 = amp exp(-|X - x|^2 / (2 sigma^2)) in the embedding distance. */
@@ -120,9 +121,10 @@ typedef struct lbw_grid lbw_grid; /* opaque, library-owned */
  * Christoffel symbols G^a = g^{bc} Gamma^a_{bc} of Sec. IV, written in lattice coordinates)
  * and allocate two population buffers on `stream`.  Rejects with LBW_EINVAL: tau != 1/2,
  * non-periodic angular axes, r <= 0 or a non-positive flare anywhere on the lattice or its
- * ghost layer, and lattices whose largest c^2 (g^{11} + g^{22} + g^{33}) + 3 cs^2 exceeds
- * 3.0 (the step operator's spectral radius exceeds 1 at 4 in flat space).  *out is set only
- * on success; release it with lbw_destroy. */
+ * ghost layer, lattices whose largest c^2 (g^{11} + g^{22} + g^{33}) + 3 cs^2 exceeds
+ * 3.0 (the step operator's spectral radius exceeds 1 at 4 in flat space), and geom_mode /
+ * equilibrium settings outside the cases their enums list.  *out is set only on success;
+ * release it with lbw_destroy. */
 lbw_status lbw_create_grid(const lbw_grid_desc* desc, void* stream, lbw_grid** out);
 
 /* Initial state at rest (J' = 0 in the sense of Eq. JShifted): rho0 = sqrt(g) P0 with P0 the
