@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from lbw_workloads import (BC_BOUNCE, BC_FREE, BC_PERIODIC, KIND_CYLINDRICAL, PREC_F32, PREC_F64, GridSpec,
+from lbw_workloads import (BC_BOUNCE, BC_FREE, BC_PERIODIC, KIND_CYLINDRICAL, PREC_F16S, PREC_F32, PREC_F64, GridSpec,
                            ensemble, pulses, probes)
 from test_gpu_parity import SPECS
 
@@ -194,6 +194,46 @@ def test_paper_pipe_is_an_open_closed_pipe():
         k = win[np.argmax(resp[win])]
         print(f"mode {m:.6f}: sweep peak {omegas[k]:.6f}")
         assert win[0] < k < win[-1], (m, omegas[win[0]], omegas[k], omegas[win[-1]])
+
+
+def _pipe_free_decay(prec, steps):
+    """The six lowest modes of the lossless paper pipe's free decay (a layer of pulses near the
+    closed end, the paper's probe), and the probe series."""
+    from paper_1705_01801_gb300 import lbw
+    from lbw_workloads import embedding, node_coords
+    spec = _paper_pipe(1.0, prec=prec)
+    pl = []
+    for i in range(1, spec.n[0], 3):
+        for j in range(spec.n[1]):
+            X = embedding(spec, *node_coords(spec, i, j, 3))
+            pl.append([X[0], X[1], X[2], 2.5, 1.0])
+    g = lbw.Grid(spec)
+    try:
+        g.init(pl)
+        g.set_probes([PAPER_PROBE], steps)
+        g.step(steps)
+        f, _ = g.spectrum(0, 6, lowest=True, rel_power=1e-3)
+        return np.sort(np.asarray(f)), g.read_probes()[0]
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(PREC_F32, 1e-5), (PREC_F16S, 5e-3)], ids=["f32", "f16"])
+def test_paper_pipe_modes_in_reduced_storage(prec, tol):
+    """At the paper's small wave speed (c = 0.1, so the forcing and the departures of the
+    populations from w P are small against the stored values) and over 65 536 steps, the
+    reduced storage forms give the FP64 run's six lowest modes of the open-closed pipe: FP32
+    within 1e-5, the 16-bit form within the 0.5 % mode bound; the FP32 probe series stays
+    within 1e-4 of the FP64 one (rounding of the coefficients and populations, no drift)."""
+    steps = 65536
+    f64, x64 = _pipe_free_decay(PREC_F64, steps)
+    f, x = _pipe_free_decay(prec, steps)
+    print(f"\nFP64 modes {np.round(f64, 6)}; prec {prec}: {np.round(f, 6)}, "
+          f"series max |diff| {np.abs(x - x64).max():.2e}")
+    assert len(f) == len(f64) == 6
+    np.testing.assert_allclose(f, f64, rtol=tol)
+    if prec == PREC_F32:
+        assert np.abs(x - x64).max() <= 1e-4 * np.abs(x64).max()
 
 
 def _paper_torus(prec=PREC_F64):
