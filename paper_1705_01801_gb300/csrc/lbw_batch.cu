@@ -126,7 +126,11 @@ __global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
   // items are claimed from a step-wide counter (the upper half of counters[2], cleared with
   // the ticket by the step's last CTA): CTAs that draw small items take more of them, so the
   // step ends when the work does (a fixed stride over the list left CTAs idle behind others
-  // with larger items; the 512-trumpet ensemble ran 20% slower)
+  // with larger items; the 512-trumpet ensemble ran 20% slower).  The producer claims the
+  // next item once it has issued the current item's last copies, a few planes before the
+  // CTA is free: neighbouring items (consecutive in the list) then start within a few
+  // microseconds of each other and march in step, so the rows and planes they share are
+  // read from DRAM once and found in L2 by the other.
   unsigned* const claim = reinterpret_cast<unsigned*>(&counters[2]) + 1;
   const unsigned sbase = smem_u32(smem_raw);
   const unsigned OFF = (128u - (sbase & 127u)) & 127u;
@@ -148,7 +152,6 @@ __global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
       unsigned* to = reinterpret_cast<unsigned*>(&A);
       for (int k = tid; k < (int)(sizeof(StepArgs<S>) / 4); k += nthr) to[k] = from[k];
     }
-    int claimed = 0;
     if (tid == 0) {
       for (int k = 0; k < NB; ++k) {
         if (!fresh) {  // the previous item left its phases behind
@@ -160,11 +163,9 @@ __global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
       }
       asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
       probe_cnt = 0;
-      claimed = (int)atomicAdd(claim, 1u);  // the next item, claimed while this one runs
     }
     fresh = false;
     __syncthreads();  // every thread has read next_it for this item
-    if (tid == 0) next_it = claimed;
     const int x0 = item.y, y0 = item.z, z0 = item.w;
     const int z1 = min(z0 + lz, A.n3);
     const bool p3 = A.bc[4] == LBW_BC_PERIODIC;
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
           issued = p;
           if (++s == NB) { s = 0; ++use; }
         }
+        next_it = (int)atomicAdd(claim, 1u);  // read by every thread after the item's last barrier
         for (int p = max(z0 - 2, issued - NB + 1); p <= issued; ++p) {
           const int k = p - (z0 - 2);
           wait_bar(full_at(k % NB), (unsigned)((k / NB) & 1));
