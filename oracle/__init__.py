@@ -44,7 +44,8 @@ PINS = {
                       "mode decay per round trip on q1 and q3 walls",
     "source/plate J'_z": "dipole plane waves at speed c, amplitude C / (cs2 + c) at c = cs, "
                          "uniform across a pipe (sqrt g)",
-    "source/ring P": "radiated profile fits J0 / Y0 of the radial Bessel equation",
+    "source/ring P": "radiated profile fits J0 / Y0 of the radial Bessel equation, also on the "
+                     "radial-wave lattice of Sec. IV.A as printed (cs2 matched to c / h_r)",
 }
 
 

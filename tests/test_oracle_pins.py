@@ -334,6 +334,64 @@ def test_ring_source_radiates_cylindrical_wave():
     assert resid([np.cos, np.sin]) > 10 * e0
 
 
+def _paper_radial_wave(n1, h_r, cs2, T=365, c=0.6, omega=0.075, r_min=1.0):
+    """Sec. IV.A's first benchmark on the oracle: n1 x 3 x 10 cells (r, theta, z), periodic in
+    theta and z, r from r_min in cells of h_r, c = 0.6, the ring source P = sin(omega t),
+    omega = 0.075, at r_min; the profile P(r) at t = 365 (the front, at c t = 219, never meets
+    the outer face).  Returns (r, P)."""
+    n = (n1, 3, 10)
+    spec = GridSpec(kind=KIND_CYLINDRICAL, n=n, h=(h_r, 2 * math.pi / 3, h_r), x0=(r_min, 0, 0),
+                    c=c, cs2=cs2, bc=(BC_FREE, BC_FREE, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC))
+    g = oracle.OracleGrid(spec)
+    g.init(np.zeros((0, 5)))
+    g.set_sources([[0, j, k] for j in range(n[1]) for k in range(n[2])], kind=0, amp=1.0, omega=omega)
+    g.step(T)
+    P = g.get_P()
+    assert np.abs(P - P[:1, :, :1]).max() <= 1e-12 * np.abs(P).max()  # no theta, z dependence
+    return r_min + (np.arange(n1) + 0.5) * h_r, P[0, :, 0]
+
+
+def _bessel_fit(r, P, k, lo, hi):
+    """Relative RMS residual of the least-squares fit of P on [lo, hi] by a J0(kr) + b Y0(kr),
+    by the order-1 pair, by a plane wave, and the best-fit k over 0.5 .. 1.5 k (ratio)."""
+    from scipy.special import j0, j1, y0, y1
+    sel = (r >= lo) & (r <= hi)
+
+    def resid(cols, kk=k):
+        A = np.stack([f(kk * r[sel]) for f in cols], 1)
+        coef, *_ = np.linalg.lstsq(A, P[sel], rcond=None)
+        return math.sqrt(((P[sel] - A @ coef) ** 2).mean() / (P[sel] ** 2).mean())
+
+    ks = np.linspace(0.5 * k, 1.5 * k, 401)
+    best = ks[int(np.argmin([resid([j0, y0], kk) for kk in ks]))] / k
+    return resid([j0, y0]), resid([j1, y1]), resid([np.cos, np.sin]), best
+
+
+@pytest.mark.parametrize("n1,h_r,cs2,tol_fit,tol_k", [
+    (100, 4.99, (0.6 / 4.99) ** 2, 0.06, 0.02),  # as printed: 100 cells over r in [1, 500]
+    (500, 1.0, 0.25, 0.02, 0.005),               # unit cells, the default cs2
+], ids=["paper-cells-cs2-matched", "unit-cells"])
+def test_paper_radial_wave(n1, h_r, cs2, tol_fit, tol_k):
+    """Sec. IV.A, Eq. TheoreticalExpresion: the radial wave from the axis is the outgoing
+    order-0 Bessel wave, a J0(kr) + b Y0(kr) with k = omega / c, at the paper's parameters.
+    With the printed 100 cells over r in [1, 500] (h_r = 4.99) the wave moves 0.12 cells per
+    step, far below the lattice's own speed cs = 1/2 at the default cs2; the force term then
+    carries almost all of the stress, and its central difference, whose error differs from
+    the streaming's, makes the wave 35 % too long (printed below).  With cs2 = (c / h_r)^2 the
+    force term vanishes along r and the profile fits.  With unit cells (500 of them) the default
+    cs2 fits to 1.2 %.  The order-1 pair and a plane wave must fit worse."""
+    r, P = _paper_radial_wave(n1, h_r, cs2)
+    k = 0.075 / 0.6
+    e0, e1, ep, kb = _bessel_fit(r, P, k, 10, 0.5 * 0.6 * 365)
+    print(f"\nh_r {h_r}, cs2 {cs2:.4f}: J0/Y0 residual {e0:.4f}, J1/Y1 {e1:.3f}, plane {ep:.3f}, best k / k {kb:.3f}")
+    assert e0 < tol_fit and abs(kb - 1) < tol_k
+    assert e1 > 1.4 * e0 and ep > 5 * e0
+    if n1 == 100:
+        r4, P4 = _paper_radial_wave(n1, h_r, 0.25)
+        e0, _, _, kb = _bessel_fit(r4, P4, k, 10, 0.5 * 0.6 * 365)
+        print(f"same lattice at cs2 = 1/4: J0/Y0 residual {e0:.3f}, best k / k {kb:.3f}")
+
+
 def test_source_kinds_impose_their_values():
     """Reading R8: after step t a P source node holds f^eq(sqrt(g) C sin(omega t), 0), a J'_z
     source node keeps its rho and carries j'_3 = sqrt(g) C sin(omega t)."""
