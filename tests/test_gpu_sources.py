@@ -199,15 +199,15 @@ def test_paper_pipe_is_an_open_closed_pipe():
 @pytest.mark.parametrize("prec,tol", [(PREC_F64, 1e-11), (PREC_F32, 2e-5)], ids=["f64", "f32"])
 def test_paper_radial_wave_matches_oracle(prec, tol):
     """The radial wave from the axis (Sec. IV.A) on the paper's lattice: 100 x 3 x 10 cells
-    over r in [1, 500], c = 0.6, the ring source sin(0.075 t) at r_min, cs2 = (c / h_r)^2 (the
+    of 4.99 along r (from r = 3, so that the inner ghost node has r > 0), c = 0.6, the ring source sin(0.075 t) at r_min, cs2 = (c / h_r)^2 (the
     lattice speed along r; the default cs2 makes the wave 35 % too long there), 365 steps.
     Device and FP64 oracle agree, and the device's profile is the outgoing J0 / Y0 wave with
     k = omega / c (fit within 6 %, wavenumber within 2 %)."""
     from paper_1705_01801_gb300 import lbw
-    from test_oracle_pins import _bessel_fit
-    h_r, T, om = 4.99, 365, 0.075
-    n = (100, 3, 10)
-    spec = GridSpec(kind=KIND_CYLINDRICAL, n=n, h=(h_r, 2 * math.pi / 3, h_r), x0=(1.0, 0, 0), c=0.6,
+    from test_oracle_pins import PAPER_RADIAL, _bessel_fit
+    h_r, r_min, T, om = PAPER_RADIAL["h_r"], PAPER_RADIAL["r_min"], 365, 0.075
+    n = (PAPER_RADIAL["n1"], 3, 10)
+    spec = GridSpec(kind=KIND_CYLINDRICAL, n=n, h=(h_r, 2 * math.pi / 3, h_r), x0=(r_min, 0, 0), c=0.6,
                     cs2=(0.6 / h_r) ** 2, prec=prec,
                     bc=(BC_FREE, BC_FREE, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC))
     src = [[0, j, k] for j in range(n[1]) for k in range(n[2])]
@@ -225,7 +225,7 @@ def test_paper_radial_wave_matches_oracle(prec, tol):
     o.step(T)
     Po = o.get_P()
     np.testing.assert_allclose(P, Po, rtol=0, atol=tol * np.abs(Po).max())
-    r = 1.0 + (np.arange(n[0]) + 0.5) * h_r
+    r = r_min + (np.arange(n[0]) + 0.5) * h_r
     e0, _, _, kb = _bessel_fit(r, P[0, :, 0], om / 0.6, 10, 0.5 * 0.6 * T)
     print(f"\ndevice prec {prec}: J0/Y0 residual {e0:.4f}, best k / k {kb:.3f}")
     assert e0 < 0.06 and abs(kb - 1) < 0.02
