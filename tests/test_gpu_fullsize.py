@@ -2,7 +2,8 @@
 times: the 256 x 256 x 512 trumpet (FP32 and FP16 storage) and the 192 x 1024 x 256 torus
 (FP32 and BF16 storage), one device step from a shared state against one FP64 oracle step at
 every node; the 512-trumpet ensemble on sampled members; the 128 x 128 disk over its full
-4000 steps."""
+4000 steps; a 512 x 1024 x 768 cylinder, whose 2.8e9 populations per buffer pass 2^31, in its
+far corner against a small oracle lattice over that corner."""
 import numpy as np
 import pytest
 
@@ -102,3 +103,46 @@ def test_disk_full_run_matches_oracle():
     finally:
         g.close()
         o.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(W.PREC_F32, 1e-5), (W.PREC_F64, 1e-11)], ids=["f32", "f64"])
+def test_lattice_beyond_2_31_populations(prec, tol):
+    """Index arithmetic past 2^31 populations (and past 2^32 bytes) per buffer: a 512 x 1024 x
+    768 cylinder (402,653,184 nodes, 2,818,572,288 populations; 11.3 GB per FP32 buffer,
+    22.5 GB in FP64) with two pulses in its far corner, one on the very last node (the last
+    rows, columns and planes, where the offsets are largest), four steps.  The field a step moves spreads two cells at most,
+    so the corner block of 44 rows x 1024 columns x 32 planes must equal an oracle lattice of
+    that block (same radii and heights, same faces on the far sides; the pulse is below 1e-11
+    at the block's near faces), and a probe in the very last node must record the same
+    series."""
+    from paper_1705_01801_gb300 import lbw
+    spec = W.cylinder(n_r=512, n_theta=1024, n_z=768, prec=prec)
+    r0, z0 = 468, 736
+    assert 7 * spec.n[0] * spec.n[1] * spec.n[2] > 2 ** 31
+    small = spec.with_(n=(spec.n[0] - r0, spec.n[1], spec.n[2] - z0), prec=W.PREC_F64,
+                       x0=(spec.x0[0] + r0 * spec.h[0], spec.x0[1], spec.x0[2] + z0 * spec.h[2]))
+    last = [spec.n[0] - 1, spec.n[1] - 1, spec.n[2] - 1]
+    pl = [[*W.embedding(spec, *W.node_coords(spec, *q)), 3.0, a] for q, a in (([500, 1000, 758], 1.0), (last, -0.5))]
+    near = [500, 1000, 760]
+    steps = 4
+    g = lbw.Grid(spec)
+    try:
+        g.init(pl)
+        g.set_probes([last, near], steps)
+        g.step(steps)
+        P = g.get_P()[z0:, r0:, :].copy()
+        series = g.read_probes()
+    finally:
+        g.close()
+    o = oracle.OracleGrid(small)
+    o.init(pl)
+    o.set_probes([[q[0] - r0, q[1], q[2] - z0] for q in (last, near)], steps)
+    o.step(steps)
+    Po = o.get_P()
+    so = o.read_probes()
+    o.close()
+    scale = np.abs(Po).max()
+    assert scale > 0.05  # the pulse is inside the block
+    np.testing.assert_allclose(P, Po, rtol=0, atol=tol * scale)
+    np.testing.assert_allclose(series, so, rtol=0, atol=tol * np.abs(so).max())
+
