@@ -182,3 +182,45 @@ def test_probe_spectrum_matches_oracle_on_polar_run():
     fsum, _ = g.spectrum(-1, 4)
     fosum, _ = oracle.spectrum(o.read_probes().sum(0), 4)
     np.testing.assert_allclose(fsum, fosum, rtol=1e-8)
+
+
+# one- and two-node extents on each axis, through the tile kernel (q2 = 64 or 128) and the
+# register-pipelined kernel (q2 = 1, 3 or 40), with walls of every kind on the short axes
+DEGENERATE = {
+    "n1=1 tile": ((1, 64, 9), (BC_BOUNCE, BC_ANTIBOUNCE, 0, 0, BC_FREE, BC_BOUNCE)),
+    "n1=2 tile": ((2, 128, 5), (BC_FREE, BC_FREE, 0, 0, 0, 0)),
+    "n3=1 tile walls": ((9, 64, 1), (BC_BOUNCE, BC_FREE, 0, 0, BC_ANTIBOUNCE, BC_BOUNCE)),
+    "n1=n3=1 tile": ((1, 64, 1), (BC_ANTIBOUNCE, BC_BOUNCE, 0, 0, BC_BOUNCE, BC_FREE)),
+    "n3=2 tile": ((3, 64, 2), (BC_BOUNCE, BC_BOUNCE, 0, 0, BC_FREE, BC_ANTIBOUNCE)),
+    "n1=1 generic": ((1, 40, 2), (BC_FREE, BC_ANTIBOUNCE, 0, 0, BC_BOUNCE, BC_FREE)),
+    "n2=1 walls": ((5, 1, 6), (BC_BOUNCE, BC_FREE, BC_ANTIBOUNCE, BC_BOUNCE, 0, 0)),
+    "n2=3 periodic": ((4, 3, 3), (0, 0, 0, 0, 0, 0)),
+}
+
+
+@pytest.mark.parametrize("name", list(DEGENERATE))
+def test_degenerate_extents_match_oracle(name):
+    """Lattices one or two nodes thick along an axis (both faces of the axis act on every
+    node; the tile kernel's first tile starts at q1 = -1 where n1 - 1 is a multiple of its
+    rows): 40 steps from seeded random populations, FP64, device against the oracle."""
+    from paper_1705_01801_gb300 import lbw
+    n, bc = DEGENERATE[name]
+    spec = GridSpec(kind=KIND_CARTESIAN, n=n, h=(1, 1, 1), x0=(0, 0, 0), c=0.4, bc=bc,
+                    damping=0.8, prec=PREC_F64)
+    f = np.random.default_rng(sum(n)).standard_normal((7, n[2], n[0], n[1]))
+    q = [[n[0] - 1, n[1] - 1, n[2] - 1], [0, 0, 0]]
+    g = lbw.Grid(spec)
+    try:
+        g.set_f(f)
+        g.set_probes(q, 40)
+        g.step(40)
+        fg, sg = g.get_f(), g.read_probes()
+    finally:
+        g.close()
+    o = oracle.OracleGrid(spec)
+    o.set_f(f)
+    o.set_probes(q, 40)
+    o.step(40)
+    fo, so = o.get_f(), o.read_probes()
+    np.testing.assert_allclose(fg, fo, rtol=0, atol=1e-11 * np.abs(fo).max())
+    np.testing.assert_allclose(sg, so, rtol=0, atol=1e-11 * np.abs(so).max())
