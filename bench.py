@@ -300,29 +300,39 @@ def run_ensemble(args):
 
 
 def surrogate_report(specs, steps):
-    """Mode targets of every member from the batched LBM (steps time steps), a 4-layer 256-wide
-    MLP trained on the first 80% of the members (device kernels, FP32), BF16-weight inference
-    on the rest: held-out mean relative error of the lowest 8 mode frequencies, the error of
-    predicting the training mean, and the per-geometry time of both."""
+    """Mode targets of every member from the batched LBM (steps time steps), 4-layer 256-wide
+    MLPs trained on the first 80% of the members (device kernels, FP32, cosine-decayed Adam),
+    BF16-weight inference on the rest: one network for the lowest 8 mode frequencies, and one
+    network per mode.  Reports the held-out mean relative error per mode, how many of the
+    lowest modes the per-mode networks give within 0.5 %, the error of predicting the training
+    mean, and the per-geometry time of the LBM and of the surrogate."""
     from paper_1705_01801_gb300 import surrogate as S
     freqs, valid, lbm_s = S.measure(specs, steps=steps, tune=True)
     X = np.stack([S.features(s) for s in specs])[valid]
     Y = freqs[valid]
     ntr = int(0.8 * len(X))
-    sur = S.Surrogate(hidden=256, depth=4, seed=0)
-    sur.fit(X[:ntr], Y[:ntr], steps=4000, batch=32, lr=1e-3)
-    t0 = time.perf_counter()
-    pred = sur.predict(X[ntr:])
-    sur_s = time.perf_counter() - t0
-    err = np.abs(pred - Y[ntr:]) / Y[ntr:]
+    out = {"members": len(specs), "valid": int(valid.sum()), "time_steps": steps,
+           "held_out": int(len(X) - ntr), "training_steps": 20000}
+    for name, per_mode in (("joint", False), ("per_mode", True)):
+        sur = S.Surrogate(hidden=256, depth=4, seed=0, per_mode=per_mode)
+        t0 = time.perf_counter()
+        sur.fit(X[:ntr], Y[:ntr], steps=20000, batch=32, lr=1e-3)
+        train_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        pred = sur.predict(X[ntr:])
+        sur_s = time.perf_counter() - t0
+        err = np.abs(pred - Y[ntr:]) / Y[ntr:]
+        per = err.mean(0)
+        within = int(np.argmax(np.append(per, 1.0) > 0.005))
+        out[name] = {"mean_rel_err": float(err.mean()),
+                     "mean_rel_err_per_mode": [round(float(x), 4) for x in per],
+                     "lowest_modes_within_0.5pct": within, "train_s": train_s,
+                     "surrogate_s_per_geometry": sur_s / max(1, len(X) - ntr),
+                     "speedup": (lbm_s / len(specs)) / (sur_s / max(1, len(X) - ntr))}
     base = np.abs(np.exp(np.log(Y[:ntr]).mean(0)) - Y[ntr:]) / Y[ntr:]
-    return {"members": len(specs), "valid": int(valid.sum()), "time_steps": steps,
-            "held_out": int(len(X) - ntr), "mean_rel_err": float(err.mean()),
-            "mean_rel_err_per_mode": [round(float(x), 4) for x in err.mean(0)],
-            "mean_predictor_rel_err": float(base.mean()),
-            "lbm_s_per_geometry": lbm_s / len(specs),
-            "surrogate_s_per_geometry": sur_s / max(1, len(X) - ntr),
-            "speedup": (lbm_s / len(specs)) / (sur_s / max(1, len(X) - ntr))}
+    out["mean_predictor_rel_err"] = float(base.mean())
+    out["lbm_s_per_geometry"] = lbm_s / len(specs)
+    return out
 
 
 def run_reference(args):

@@ -60,14 +60,26 @@ def measure(specs, steps: int, n_modes: int = 8, rel_power: float = 1e-3, tune: 
 
 
 class Surrogate:
-    """Standardised inputs and outputs around an lbw.MLP (4 weight layers, 256 wide)."""
+    """Standardised inputs and outputs around lbw.MLP networks (4 weight layers, 256 wide):
+    one network for all modes, or (per_mode) one network per mode, so that the smooth lowest
+    modes do not share capacity with the higher ones, whose order changes where mode families
+    cross."""
 
     def __init__(self, in_dim: int = len(FEATURE_NAMES), out_dim: int = 8, hidden: int = 256,
-                 depth: int = 4, seed: int = 0):
-        self.net = lbw.MLP(in_dim, hidden=hidden, depth=depth, out_dim=out_dim, seed=seed)
+                 depth: int = 4, seed: int = 0, per_mode: bool = False):
+        self.per_mode = per_mode
+        if per_mode:
+            self.nets = [lbw.MLP(in_dim, hidden=hidden, depth=depth, out_dim=1, seed=seed * out_dim + k)
+                         for k in range(out_dim)]
+        else:
+            self.nets = [lbw.MLP(in_dim, hidden=hidden, depth=depth, out_dim=out_dim, seed=seed)]
         self.mx = self.sx = self.my = self.sy = None
 
-    def fit(self, X, Y, steps: int = 4000, batch: int = 64, lr: float = 1e-3, seed: int = 0):
+    def fit(self, X, Y, steps: int = 4000, batch: int = 64, lr: float = 1e-3, seed: int = 0,
+            decay_chunks: int = 20):
+        """Adam on the standardised log-frequencies; the learning rate follows a cosine decay
+        from lr, held constant over each of decay_chunks equal runs of steps (1: constant).
+        Returns the minibatch loss curve of every network, shape (networks, steps)."""
         X = np.asarray(X, np.float64)
         Y = np.log(np.asarray(Y, np.float64))  # frequencies are positive and span decades
         self.mx, self.sx = X.mean(0), X.std(0) + 1e-12
@@ -78,11 +90,21 @@ class Surrogate:
         per_epoch = max(1, len(Xn) // batch)
         order = np.concatenate([rng.permutation(len(Xn))[: per_epoch * batch]
                                 for _ in range(math.ceil(steps / per_epoch))])[: steps * batch]
-        return self.net.train(Xn, Yn, order, batch, lr)
+        chunks = max(1, min(decay_chunks, steps))
+        curves = []
+        for k, net in enumerate(self.nets):
+            T = np.ascontiguousarray(Yn[:, k:k + 1] if self.per_mode else Yn)
+            curve = []
+            for c in range(chunks):
+                lo, hi = steps * c // chunks, steps * (c + 1) // chunks
+                rate = lr * 0.5 * (1.0 + math.cos(math.pi * c / chunks)) if chunks > 1 else lr
+                curve.append(net.train(Xn, T, order[lo * batch:hi * batch], batch, rate))
+            curves.append(np.concatenate(curve))
+        return np.stack(curves)
 
     def predict(self, X, bf16: bool = True):
         Xn = ((np.asarray(X, np.float64) - self.mx) / self.sx).astype(np.float32)
-        Yn = self.net.predict_bf16(Xn) if bf16 else self.net.forward(Xn)
+        Yn = np.concatenate([net.predict_bf16(Xn) if bf16 else net.forward(Xn) for net in self.nets], axis=1)
         return np.exp(Yn.astype(np.float64) * self.sy + self.my)
 
 
