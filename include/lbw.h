@@ -283,13 +283,24 @@ lbw_status lbw_batch_spectrum_lowest(lbw_batch* b, int32_t k, double rel_power, 
 /* Member's populations as doubles (7 x N of that member). */
 lbw_status lbw_batch_get_populations(lbw_batch* b, int32_t member, double* host_f);
 
-/* Autotuner: times candidate launch shapes (rows per tile 4/8/16, planes per q3 segment
- * 16/32/64, CTAs per SM 1/2/4) for trial_steps steps each and keeps the fastest.  With a
- * cache_path (JSON lines), a shape stored for the same ensemble signature is reused without
- * timing and a new choice is appended.  The trial steps run on the ensemble's buffers: call
- * it before lbw_batch_init.  A text report of the timings goes to report (may be NULL). */
+/* Autotuner: times candidate launch shapes for trial_steps steps each and keeps the fastest.
+ * Ensembles whose members all wrap in q2 and have walls in q1 run the TMA-staged kernel
+ * (tile rows 4 or 7 of 64 columns, or 0: full-row tiles, each member's whole rows with a
+ * height that follows its row length, offered when every member fits one and the storage
+ * is 32- or 64-bit; CTAs per SM 1/2); others the register-pipelined kernel (rows 4/8/16,
+ * CTAs per SM 1/2/4); planes per q3 segment 16/32/64 for both.  With a cache_path (JSON
+ * lines), a shape stored for the same ensemble signature is reused without timing and a new
+ * choice is appended.  The trial steps run on the ensemble's buffers: call it before
+ * lbw_batch_init.  A text report of the timings goes to report (may be NULL). */
 lbw_status lbw_batch_tune(lbw_batch* b, int32_t trial_steps, const char* cache_path, char* report,
                           int32_t report_cap);
+
+/* Sets the launch shape instead of the autotuner: tile_rows (one of the values the autotuner
+ * offers this ensemble, see lbw_batch_tune), seg_planes >= 1, ctas_per_sm >= 1 and at most
+ * what the kernel can keep resident.  LBW_EINVAL for a shape this ensemble cannot run.  The
+ * populations are kept; the step kernels differ only in how they stage them (every shape
+ * gives the same numbers). */
+lbw_status lbw_batch_set_shape(lbw_batch* b, int32_t tile_rows, int32_t seg_planes, int32_t ctas_per_sm);
 
 /* Total nodes and the launch shape in use (any pointer may be NULL). */
 lbw_status lbw_batch_info(lbw_batch* b, int64_t* total_nodes, int32_t* tile_rows, int32_t* seg_planes,

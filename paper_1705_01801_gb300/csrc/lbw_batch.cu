@@ -524,8 +524,429 @@ __global__ void __launch_bounds__(32 * (BY + 3)) batch_tma_kernel(
   finish_step(counters, nprobe, cap, gridDim.x);
 }
 
+// ---------------------------------------------------------------- full-row ensemble --------
+//
+// When every member's row fits a tile, a tile spans whole rows: ROWS = BY_m + 2 staged rows
+// of the member's n2 data columns, with the tile's nodes laid out row-major over the consumer
+// lanes (two q2-adjacent nodes per lane; with an odd n2 the last pair of a row carries one
+// phantom node, computed and discarded).  The periodic q2 wrap then lies inside the tile: the
+// pulls across it and the q2 gradient read the other end of the same staged row, so no ghost
+// column is read or written, one tensor copy stages a population (ROWS x n2 rounded up to 16
+// bytes, the box of the member's own tensor map), and no lane is left idle by a ragged last
+// q2 tile.  The tile height follows the member (narrow rows give tall tiles).  The staging
+// pipeline, slot regrouping, faces and collision are those of batch_tma_kernel.  32- and
+// 64-bit storage.
+constexpr int kRowWarps = 9;                   // consumer warps
+constexpr int kRowNodes = kRowWarps * 32 * 2;  // nodes of a tile plane
+constexpr int kRowCap = 648;                   // staged elements of a population plane
+constexpr int kRowMaxBY = 16;                  // tile rows at most (coefficient slots)
+constexpr int kRowMinBY = 3;                   // fewer would put a halo row on a q1 face
+
+// Staged rows of a member's full-row tile (BY_m + 2), 0 when the member cannot use one.
+inline int row_tile_rows(int n2, size_t es) {
+  const int v = (int)(16 / es), n2w = n2 + (n2 & 1), bw = (n2 + v - 1) / v * v;
+  if (bw > 256) return 0;
+  const int rows = std::min(std::min(kRowNodes / n2w, kRowCap / bw), kRowMaxBY + 2);
+  return rows - 2 >= kRowMinBY ? rows : 0;
+}
+
+template <typename S>
+struct BatchRowLayout {
+  using R = typename Store<S>::R;
+  static constexpr int POPB = ((kRowCap * (int)sizeof(S)) + 127) / 128 * 128;
+  static constexpr int SLOTB = 7 * POPB;
+  static constexpr int TABB = ((kRowMaxBY * T_SLOTS * (int)sizeof(R)) + 127) / 128 * 128;
+  static constexpr int RHOB = ((3 * kRowNodes * (int)sizeof(R)) + 127) / 128 * 128;
+};
+
+template <typename S>
+constexpr size_t batch_row_smem() {
+  using L = BatchRowLayout<S>;
+  return 128 + 128 + 5 * (size_t)L::SLOTB + L::RHOB + 5 * (size_t)L::TABB;
+}
+
+// items: (member, BY_m, first interior row y0 (may be -1), z0)
+template <typename S>
+__global__ void __launch_bounds__(32 * (kRowWarps + 1), sizeof(S) == 4 ? 2 : 1) batch_row_kernel(
+    const StepArgs<S>* __restrict__ members, const CUtensorMap* __restrict__ maps, int src,
+    const int4* __restrict__ items, int n_items, int lz, unsigned long long* counters, int nprobe,
+    long long cap) {
+  using R = typename Store<S>::R;
+  using L = BatchRowLayout<S>;
+  static_assert(sizeof(S) >= 4, "the full-row tile regroups slots: 32- and 64-bit storage");
+  constexpr int NPT = 2, NB = 5, NCW = kRowWarps;
+  constexpr int ES = (int)sizeof(S), RS = (int)sizeof(R), V = 16 / ES;
+  constexpr int POPB = L::POPB, SLOTB = L::SLOTB, TABB = L::TABB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) StepArgs<S> A;
+  __shared__ int probe_list[kMaxProbes];
+  __shared__ int probe_cnt;
+  __shared__ int abort_flag;
+  __shared__ int next_it;
+  __shared__ unsigned long long t_sample;
+
+  const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane, nthr = 32 * (NCW + 1);
+  // items are claimed as in batch_tma_kernel (the producer claims the next one once it has
+  // issued the current item's last copies)
+  unsigned* const claim = reinterpret_cast<unsigned*>(&counters[2]) + 1;
+  const unsigned sbase = smem_u32(smem_raw);
+  const unsigned OFF = (128u - (sbase & 127u)) & 127u;
+  const unsigned SL = OFF + 128, RHO = SL + NB * SLOTB, TAB = RHO + L::RHOB;
+  auto full_at = [&](int k) { return sbase + OFF + 8u * k; };
+  auto empty_at = [&](int k) { return sbase + OFF + 8u * (NB + k); };
+  if (tid == 0) {
+    abort_flag = 0;
+    t_sample = counters[1];
+    next_it = (int)atomicAdd(claim, 1u);
+  }
+  __syncthreads();
+
+  bool fresh = true;
+  for (int it = next_it; it < n_items;) {
+    const int4 item = items[it];
+    {
+      const unsigned* from = reinterpret_cast<const unsigned*>(members + item.x);
+      unsigned* to = reinterpret_cast<unsigned*>(&A);
+      for (int k = tid; k < (int)(sizeof(StepArgs<S>) / 4); k += nthr) to[k] = from[k];
+    }
+    if (tid == 0) {
+      for (int k = 0; k < NB; ++k) {
+        if (!fresh) {
+          mbar_inval(full_at(k));
+          mbar_inval(empty_at(k));
+        }
+        mbar_init_count(full_at(k), 1);
+        mbar_init_count(empty_at(k), NCW);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+      probe_cnt = 0;
+    }
+    fresh = false;
+    __syncthreads();  // every thread has read next_it for this item
+    const int BYm = item.y, y0 = item.z, z0 = item.w, ROWS = BYm + 2;
+    const int z1 = min(z0 + lz, A.n3);
+    const bool p3 = A.bc[4] == LBW_BC_PERIODIC;
+    const int n2 = A.n2, n2w = n2 + (n2 & 1), BW = (n2 + V - 1) / V * V;
+    if (tid < A.nprobe) {
+      const int pq1 = A.probe_q[3 * tid], pq3 = A.probe_q[3 * tid + 2];
+      if (pq1 >= y0 && pq1 < y0 + BYm && pq3 >= z0 && pq3 < z1) probe_list[atomicAdd(&probe_cnt, 1)] = tid;
+    }
+    __syncthreads();
+    const CUtensorMap* tm_f = maps + 3 * item.x + src;
+    const CUtensorMap* tm_t = maps + 3 * item.x + 2;
+
+    auto wait_bar = [&](unsigned bar, unsigned parity) -> bool {
+      long long n = 0;
+      while (!mbar_try_wait(bar, parity)) {
+        if (++n > kWaitLimit) {
+          abort_flag = 1;
+          A.counters[3] = 1;
+          return false;
+        }
+      }
+      return true;
+    };
+
+    if (w == NCW) {  // ---------------------------------------------------------- producer
+      if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const unsigned tx_pop = (unsigned)(ROWS * BW * ES);
+        const int xg = A.col0;  // the first data column of a stored row
+        int s = 0, use = 0, issued = z0 - 3;
+        for (int p = z0 - 2; p <= z1; ++p) {
+          if (use > 0 && !wait_bar(empty_at(s), (unsigned)((use - 1) & 1))) break;
+          const unsigned bar = full_at(s);
+          const unsigned base = sbase + SL + s * SLOTB;
+          const int pg = resolve(p, A.n3, p3);
+          if (p == z0 - 2) {
+            // population 5 of this plane; population 6 of the q3 = 0 face when z0 - 1 is it
+            const int pn = (!p3 && z0 == 1) ? 0 : -1;
+            mbar_expect_tx(bar, (pg < 0 ? 0u : tx_pop) + (pn >= 0 ? tx_pop : 0u));
+            if (pg >= 0) tma_load_4d(base + 5 * POPB, tm_f, xg, y0 - 1, pg, 5, bar);
+            if (pn >= 0) tma_load_4d(base + 6 * POPB, tm_f, xg, y0 - 1, pn, 6, bar);
+          } else {
+            const int pn = resolve(p + 1, A.n3, p3);
+            const bool tab = pg >= 0 && p >= z0 && p < z1;
+            mbar_expect_tx(bar, (pg >= 0 ? 6 * tx_pop : 0u) + (pn >= 0 ? tx_pop : 0u) +
+                                    (tab ? (unsigned)(BYm * T_SLOTS * RS) : 0u));
+#pragma unroll 1
+            for (int i = 0; i < 7; ++i) {
+              const int pi = i == 6 ? pn : pg;
+              if (pi >= 0) tma_load_4d(base + i * POPB, tm_f, xg, y0 - 1 - xi1_of(i), pi, i, bar);
+            }
+            if (tab) tma_load_3d(sbase + TAB + s * TABB, tm_t, 0, y0, pg, bar);
+          }
+          issued = p;
+          if (++s == NB) { s = 0; ++use; }
+        }
+        next_it = (int)atomicAdd(claim, 1u);  // read by every thread after the item's last barrier
+        for (int p = max(z0 - 2, issued - NB + 1); p <= issued; ++p) {
+          const int k = p - (z0 - 2);
+          wait_bar(full_at(k % NB), (unsigned)((k / NB) & 1));
+        }
+      }
+    } else {  // -------------------------------------------------------------------- consumers
+      // this lane's node pair: flattened index 2 (w * 32 + lane) over ROWS x n2w, row-major
+      const int nd = 2 * (w * 32 + lane);
+      const bool active = nd < ROWS * n2w;
+      const int row = active ? nd / n2w : ROWS - 1, col = active ? nd % n2w : 0;
+      const int q1 = y0 - 1 + row;
+      const bool interior = row >= 1 && row <= BYm;
+      const bool rowin = q1 >= 0 && q1 < A.n1;
+      const bool owner = active && interior && rowin;
+      const bool odd_last = col + 1 == n2;  // the pair's second node is a phantom (odd n2)
+      auto wall = [&](int b) -> R { return b == LBW_BC_BOUNCE ? A.damping : R(-1); };
+      auto ld1 = [&](unsigned off) -> R { return Store<S>::ld_smem(reinterpret_cast<const S*>(smem_raw + off)); };
+      auto ldv = [&](unsigned off, R (&o)[NPT]) { VecN<S, NPT>::ld(reinterpret_cast<const S*>(smem_raw + off), o); };
+      auto ldr = [&](unsigned off) -> R { return *reinterpret_cast<const R*>(smem_raw + off); };
+
+      // staged offsets: populations 0, 3, 4, 5, 6 at (row, col); 1 / 2 at the pull or at the
+      // q1-face rule (a face row reads the staged row next to it, never a halo row: tiles
+      // have >= 3 interior rows and start at q1 = -1 where a halo row would sit on a face)
+      const unsigned own = (unsigned)((row * BW + col) * ES);
+      unsigned o1 = POPB + own, o2 = 2 * POPB + own;
+      R m1 = R(1), m2 = R(1);
+      if (rowin && q1 == 0) {
+        const int b = A.bc[0];
+        if (b == LBW_BC_FREE) o1 = POPB + own + BW * ES;
+        else { o1 = 2 * POPB + own - BW * ES; m1 = wall(b); }
+      }
+      if (rowin && q1 == A.n1 - 1) {
+        const int b = A.bc[1];
+        if (b == LBW_BC_FREE) o2 = 2 * POPB + own - BW * ES;
+        else { o2 = POPB + own + BW * ES; m2 = wall(b); }
+      }
+      // q2 neighbours across the periodic wrap, inside the same staged row: column cl left of
+      // the pair, cr right of it, column 0 for the last node of an odd row
+      const int cl = col == 0 ? n2 - 1 : col - 1;
+      const int cr = col + 2 >= n2 ? col + 2 - n2 : col + 2;
+      const unsigned o3e = (unsigned)(3 * POPB + (row * BW + cl) * ES);
+      const unsigned o4e = (unsigned)(4 * POPB + (row * BW + cr) * ES);
+      const unsigned o4w = (unsigned)(4 * POPB + row * BW * ES);
+      const bool f5_own = A.bc[4] == LBW_BC_FREE, f6_own = A.bc[5] == LBW_BC_FREE;
+      const R m5_face = A.bc[4] == LBW_BC_FREE ? R(1) : wall(A.bc[4]);
+      const R m6_face = A.bc[5] == LBW_BC_FREE ? R(1) : wall(A.bc[5]);
+      // rho planes: ROWS rows of n2w values (the phantom column included, never read)
+      const unsigned myrho = (unsigned)((row * n2w + col) * RS);
+      const unsigned lrho = (unsigned)((row * n2w + cl) * RS), rrho = (unsigned)((row * n2w + cr) * RS);
+      const unsigned wrho = (unsigned)(row * n2w * RS);
+      constexpr unsigned PLANE = (unsigned)(kRowNodes * RS);
+
+      bool has_probe = false;
+      if (owner && t_sample < (unsigned long long)A.cap)
+        for (int s = 0; s < probe_cnt; ++s) has_probe |= A.probe_q[3 * probe_list[s]] == q1;
+
+      R fA[7][NPT], fB[7][NPT], rA[NPT], rB[NPT], rC[NPT];
+      const long long row_stride = (long long)A.n1 * A.pitch;
+      S* const dst_z0 = A.fout + ((long long)z0 * A.n1 + (owner ? q1 : 0)) * A.pitch + A.col0 + col;
+
+      // step A of pulled plane u (slot sl0: populations 0-5 of u and 6 of u + 1; slot slm:
+      // population 5 of u - 1 and 6 of u), rho into rr and (wr) into rho plane rbu
+      auto stepA = [&](int u, R (&f)[7][NPT], R (&rr)[NPT], int slm, int sl0, int rbu, bool wr) {
+        const bool zlo = !p3 && u == 0, zhi = !p3 && u == A.n3 - 1;
+        const bool zghost = !p3 && (u < 0 || u >= A.n3);
+        const unsigned S0 = SL + sl0 * SLOTB, SM = SL + slm * SLOTB;
+        const unsigned B5 = zlo ? (f5_own ? S0 + 5 * POPB : SM + 6 * POPB) : SM + 5 * POPB;
+        const unsigned B6 = zhi ? (f6_own ? SM + 6 * POPB : S0 + 5 * POPB) : S0 + 6 * POPB;
+        const R m5 = zlo ? m5_face : R(1), m6 = zhi ? m6_face : R(1);
+        R t3[NPT], t4[NPT];
+        ldv(S0 + own, f[0]);
+        ldv(S0 + o1, f[1]);
+        ldv(S0 + o2, f[2]);
+        ldv(S0 + 3 * POPB + own, t3);
+        ldv(S0 + 4 * POPB + own, t4);
+        ldv(B5 + own, f[5]);
+        ldv(B6 + own, f[6]);
+        f[3][0] = ld1(S0 + o3e);
+        f[3][1] = t3[0];
+        f[4][0] = odd_last ? ld1(S0 + o4w) : t4[1];
+        f[4][1] = ld1(S0 + o4e);
+        const bool ghost = zghost || !rowin;
+        if constexpr (sizeof(R) == 4) {
+          float2 F[7];
+#pragma unroll
+          for (int i = 0; i < 7; ++i) F[i] = f2(f[i][0], f[i][1]);
+          F[1] = mul2(bc2(m1), F[1]);
+          F[2] = mul2(bc2(m2), F[2]);
+          F[5] = mul2(bc2(m5), F[5]);
+          F[6] = mul2(bc2(m6), F[6]);
+          f[1][0] = F[1].x; f[1][1] = F[1].y;
+          f[2][0] = F[2].x; f[2][1] = F[2].y;
+          f[5][0] = F[5].x; f[5][1] = F[5].y;
+          f[6][0] = F[6].x; f[6][1] = F[6].y;
+          const float2 sum = add2(add2(add2(F[0], F[1]), add2(F[2], F[3])), add2(add2(F[4], F[5]), F[6]));
+          rr[0] = ghost ? R(0) : sum.x;
+          rr[1] = ghost ? R(0) : sum.y;
+        } else {
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+            f[1][k] *= m1; f[2][k] *= m2; f[5][k] *= m5; f[6][k] *= m6;
+            const R sum = ((f[0][k] + f[1][k]) + (f[2][k] + f[3][k])) + ((f[4][k] + f[5][k]) + f[6][k]);
+            rr[k] = ghost ? R(0) : sum;
+          }
+        }
+        if (wr && active) VecN<R, NPT>::st(reinterpret_cast<R*>(smem_raw + RHO + rbu * PLANE + myrho), rr);
+      };
+
+      // step B: collide plane zc (populations fc, rho rp / rc / rn of planes zc - 1 / zc / zc + 1)
+      auto stepB = [&](int zc, R (&fc)[7][NPT], const R (&rp)[NPT], const R (&rc)[NPT],
+                       const R (&rn)[NPT], int slz, int rbz) {
+        const unsigned pl = RHO + rbz * PLANE;
+        R ru[NPT], rd[NPT];
+        VecN<R, NPT>::ld(reinterpret_cast<const R*>(smem_raw + pl + myrho + n2w * RS), ru);
+        VecN<R, NPT>::ld(reinterpret_cast<const R*>(smem_raw + pl + myrho - n2w * RS), rd);
+        const R rl[NPT] = {ldr(pl + lrho), rc[0]};
+        const R rrt[NPT] = {odd_last ? ldr(pl + wrho) : rc[1], ldr(pl + rrho)};
+        const unsigned T = TAB + slz * TABB + (row - 1) * (T_SLOTS * RS);
+        R c[T_SLOTS];
+#pragma unroll
+        for (int k = 0; k < T_SLOTS; k += 4) {
+          if (RS == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(smem_raw + T + k * RS);
+            c[k] = v.x; c[k + 1] = v.y; c[k + 2] = v.z; c[k + 3] = v.w;
+          } else {
+            const double2 v0 = *reinterpret_cast<const double2*>(smem_raw + T + k * RS);
+            const double2 v1 = *reinterpret_cast<const double2*>(smem_raw + T + (k + 2) * RS);
+            c[k] = v0.x; c[k + 1] = v0.y; c[k + 2] = v1.x; c[k + 3] = v1.y;
+          }
+        }
+        if constexpr (sizeof(R) == 4) {
+          const float2 A1P = bc2(-c[T_A1P]), A1M = bc2(c[T_A1M]), C13P = bc2(-c[T_C13P]),
+                       C13M = bc2(c[T_C13M]), S1 = bc2(-c[T_S1]), B13P = bc2(-c[T_B13P]),
+                       B13M = bc2(c[T_B13M]), C33P = bc2(-c[T_C33P]), C33M = bc2(c[T_C33M]),
+                       S3 = bc2(-c[T_S3]), H22 = bc2(c[T_H22]), MG1 = bc2(c[T_MG1]),
+                       MG3 = bc2(c[T_MG3]), CS2 = bc2(A.cs2), W0 = bc2(A.two_w0), HALF = bc2(0.5f),
+                       MHALF = bc2(-0.5f);
+          const float2 rho = f2(rc[0], rc[1]);
+          const float2 u = f2(ru[0], ru[1]), d = f2(rd[0], rd[1]);
+          const float2 n = f2(rn[0], rn[1]), p = f2(rp[0], rp[1]);
+          const float2 nD1 = fma2(S1, rho, fma2(C13M, p, fma2(C13P, n, fma2(A1M, d, mul2(A1P, u)))));
+          const float2 nD3 = fma2(S3, rho, fma2(C33M, p, fma2(C33P, n, fma2(B13M, d, mul2(B13P, u)))));
+          const float2 D2 = mul2(H22, sub2(f2(rrt[0], rrt[1]), f2(rl[0], rl[1])));
+          float2 F[7];
+#pragma unroll
+          for (int i = 0; i < 7; ++i) F[i] = f2(fc[i][0], fc[i][1]);
+          const float2 j1 = fma2(HALF, fma2(MG1, rho, nD1), sub2(F[1], F[2]));
+          const float2 j2 = fma2(MHALF, D2, sub2(F[3], F[4]));
+          const float2 j3 = fma2(HALF, fma2(MG3, rho, nD3), sub2(F[5], F[6]));
+          const float2 e = mul2(CS2, rho);
+          float2 o[7];
+          o[0] = sub2(mul2(W0, rho), F[0]);
+          o[1] = sub2(add2(e, j1), F[1]);
+          o[2] = sub2(sub2(e, j1), F[2]);
+          o[3] = sub2(add2(e, j2), F[3]);
+          o[4] = sub2(sub2(e, j2), F[4]);
+          o[5] = sub2(add2(e, j3), F[5]);
+          o[6] = sub2(sub2(e, j3), F[6]);
+#pragma unroll
+          for (int i = 0; i < 7; ++i) {
+            fc[i][0] = o[i].x;
+            fc[i][1] = o[i].y;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+            const R rho = rc[k];
+            const R D1 = c[T_A1P] * ru[k] - c[T_A1M] * rd[k] + c[T_C13P] * rn[k] - c[T_C13M] * rp[k] +
+                         c[T_S1] * rho;
+            const R D3 = c[T_B13P] * ru[k] - c[T_B13M] * rd[k] + c[T_C33P] * rn[k] - c[T_C33M] * rp[k] +
+                         c[T_S3] * rho;
+            const R D2 = c[T_H22] * (rrt[k] - rl[k]);
+            const R j1 = (fc[1][k] - fc[2][k]) + R(0.5) * (c[T_MG1] * rho - D1);
+            const R j2 = (fc[3][k] - fc[4][k]) - R(0.5) * D2;
+            const R j3 = (fc[5][k] - fc[6][k]) + R(0.5) * (c[T_MG3] * rho - D3);
+            const R e = A.cs2 * rho;
+            fc[0][k] = A.two_w0 * rho - fc[0][k];
+            fc[1][k] = e + j1 - fc[1][k];
+            fc[2][k] = e - j1 - fc[2][k];
+            fc[3][k] = e + j2 - fc[3][k];
+            fc[4][k] = e - j2 - fc[4][k];
+            fc[5][k] = e + j3 - fc[5][k];
+            fc[6][k] = e - j3 - fc[6][k];
+          }
+        }
+        S* dst = dst_z0 + (long long)(zc - z0) * row_stride;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+          if (odd_last) Store<S>::st(dst, fc[i][0]);
+          else VecN<S, NPT>::st(dst, fc[i]);
+          dst += A.ps;
+        }
+        if (has_probe) {
+          for (int s = 0; s < probe_cnt; ++s) {
+            const int k = probe_list[s];
+            const int dq = A.probe_q[3 * k + 1] - col;
+            if (A.probe_q[3 * k] == q1 && dq >= 0 && dq < NPT && col + dq < n2 && A.probe_q[3 * k + 2] == zc)
+              A.series[(long long)k * A.cap + t_sample] = (double)(dq == 0 ? rc[0] : rc[1]) * (double)c[T_INVSG];
+          }
+        }
+      };
+
+      // every lane runs the same loop (halo, interior and idle lanes share warps); step B runs
+      // on the lanes that own lattice nodes
+      bool ok = wait_bar(full_at(0), 0) && wait_bar(full_at(1), 0);
+      if (ok && owner) stepA(z0 - 1, fB, rA, 0, 1, 2, false);
+      if (lane == 0) mbar_arrive(empty_at(0));
+      ok = ok && wait_bar(full_at(2), 0);
+      if (ok) stepA(z0, fA, rB, 1, 2, 0, true);
+      if (lane == 0) mbar_arrive(empty_at(1));
+      ok = !named_sync_or(1, NCW * 32, !ok || abort_flag);
+      int sz = 2, s1 = 3, s2 = 4, uw = 0, rbz = 0, rb1 = 1;
+      auto advance = [&]() {
+        rbz = rb1;
+        rb1 = rb1 == 2 ? 0 : rb1 + 1;
+        sz = s1;
+        s1 = s2;
+        s2 = s2 == NB - 1 ? 0 : s2 + 1;
+        if (s1 == 0) ++uw;
+      };
+      auto iter = [&](int zz, R (&fc)[7][NPT], R (&fn)[7][NPT], const R (&rp)[NPT],
+                      const R (&rc)[NPT], R (&rn)[NPT]) {
+        const bool in = wait_bar(full_at(s1), (unsigned)(uw & 1));
+        if (in) stepA(zz + 1, fn, rn, sz, s1, rb1, true);
+        const bool go = !named_sync_or(1, NCW * 32, !in || abort_flag);
+        if (go && owner) stepB(zz, fc, rp, rc, rn, sz, rbz);
+        if (lane == 0) mbar_arrive(empty_at(sz));
+        advance();
+        return go;
+      };
+      int z = z0;
+      for (; ok && z + 1 < z1; z += 2) {
+        ok = iter(z, fA, fB, rA, rB, rC);
+        if (!ok) break;
+        ok = iter(z + 1, fB, fA, rB, rC, rA);
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+          const R t = rA[k];
+          rA[k] = rC[k];
+          rB[k] = t;
+        }
+      }
+      if (ok && z < z1) ok = iter(z, fA, fB, rA, rB, rC);
+    }
+    __syncthreads();  // item done: the producer has drained, the next item re-uses everything
+    if (abort_flag) break;
+    it = next_it;
+  }
+  finish_step(counters, nprobe, cap, gridDim.x);
+}
+
+// Ghost columns of padded rows from the data columns they copy (G on each side: ghost-left =
+// the last G data columns, ghost-right = the first G), for a member's buffer f: the full-row
+// kernel does not keep them, the 64-column kernel reads them.
+template <typename S>
+__global__ void ghost_fill_kernel(S* __restrict__ f, long long rows, int pitch, int n2, int G) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < rows * 2 * G;
+       k += (long long)gridDim.x * blockDim.x) {
+    S* row = f + (k / (2 * G)) * pitch;
+    const int j = (int)(k % (2 * G));
+    if (j < G) row[j] = row[n2 + j];
+    else row[n2 + j] = row[j];
+  }
+}
+
 struct Shape {
-  int by = 8;    // tile rows (register-pipelined: CTA = 32 x by threads; TMA: 4 or 7)
+  int by = 8;    // tile rows (register-pipelined: CTA = 32 x by threads; TMA: 4 or 7, 0 = full rows)
   int lz = 32;   // planes per q3 segment
   int cps = 2;   // CTAs per SM of the persistent grid
 };
@@ -591,6 +1012,7 @@ struct lbw_batch {
   bool initialised = false;
   long long total_nodes = 0;
   bool tma = false;              // padded members on the TMA-staged kernel
+  bool rowk = false;             // ... and every member fits a full-row tile (shape.by == 0)
   void* maps = nullptr;          // device: per member tensor maps (buffer 0, buffer 1, table)
   // harmonic sources of all members (offsets from the buffer base), applied after each step
   int nsrc = 0, src_kind = 0;
@@ -684,8 +1106,26 @@ auto prec_dispatch(int prec, F&& f) {
   }
 }
 
-// resident CTAs per SM of the TMA-staged kernel with `by` rows (0 when it cannot run)
+// resident CTAs per SM of the full-row kernel (0 when it cannot run)
+int row_cps(int prec) {
+  auto occ = [](auto kern, size_t smem) {
+    int per = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * (kRowWarps + 1), smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return per;
+  };
+  if (prec == LBW_F32) return occ(batch_row_kernel<float>, batch_row_smem<float>());
+  if (prec == LBW_F64) return occ(batch_row_kernel<double>, batch_row_smem<double>());
+  return 0;
+}
+
+// resident CTAs per SM of the TMA-staged kernel with `by` rows (0 when it cannot run; by = 0:
+// the full-row kernel)
 int tma_cps(int prec, int by) {
+  if (by == 0) return row_cps(prec);
   return prec_dispatch(prec, [&](auto tag) {
     using S = decltype(tag);
     return batch_tma_dispatch<S>(by, [&](auto kern, size_t smem) {
@@ -723,13 +1163,17 @@ lbw_status build_batch_maps(lbw_batch* b, int by) {
     const uint64_t P = (uint64_t)g.pitch, n1 = (uint64_t)g.d.n[0], n3 = (uint64_t)g.d.n[2];
     const uint64_t dims[4] = {P, n1, n3, 7};
     const uint64_t strides[3] = {P * es, P * n1 * es, P * n1 * n3 * es};
-    const uint32_t box[4] = {(uint32_t)(kTmaBatchBX + 2 * g.col0), (uint32_t)(by + 2), 1, 1};
+    // by = 0: full-row tiles, the member's n2 data columns (rounded up to 16 bytes) x its rows
+    const int v = (int)(16 / es), rows = by == 0 ? row_tile_rows(g.d.n[1], es) : by + 2;
+    if (rows < 3) return fail(LBW_EINVAL, "ensemble member " + std::to_string(m) + " does not fit a full-row tile");
+    const uint32_t box[4] = {(uint32_t)(by == 0 ? (g.d.n[1] + v - 1) / v * v : kTmaBatchBX + 2 * g.col0),
+                             (uint32_t)rows, 1, 1};
     for (int k = 0; k < 2; ++k)
       if (!encode_tiled_map(&h[3 * m + k], b->prec, 4, g.f[k], dims, strides, box))
         return fail(LBW_ECUDA, "tensor map of ensemble member " + std::to_string(m));
     const uint64_t tdims[3] = {(uint64_t)T_SLOTS, n1, n3};
     const uint64_t tstr[2] = {(uint64_t)T_SLOTS * rs, (uint64_t)T_SLOTS * rs * n1};
-    const uint32_t tbox[3] = {(uint32_t)T_SLOTS, (uint32_t)by, 1};
+    const uint32_t tbox[3] = {(uint32_t)T_SLOTS, (uint32_t)(rows - 2), 1};
     if (!encode_tiled_map(&h[3 * m + 2], rprec, 3, g.table, tdims, tstr, tbox))
       return fail(LBW_ECUDA, "table tensor map of ensemble member " + std::to_string(m));
   }
@@ -743,10 +1187,19 @@ lbw_status build_batch_maps(lbw_batch* b, int by) {
 // work list for the current shape: items of each member in (q3 segment, q1 tile, q2 tile)
 // order, so consecutive CTAs hold spatial neighbours.  TMA tiles are 64 columns wide and
 // start at q1 = -1 when (n1 - 1) is a multiple of the tile rows (no halo row on a face).
+// Full-row tiles (shape.by == 0) have the member's own row count: items (member, rows, y0, z0).
 lbw_status build_items(lbw_batch* b) {
   std::vector<int4> items;
   for (int m = 0; m < b->n; ++m) {
     const lbw_grid_desc& d = b->views[m].d;
+    if (b->tma && b->shape.by == 0) {
+      const int by = row_tile_rows(d.n[1], b->views[m].elem) - 2;
+      if (by < kRowMinBY) return fail(LBW_EINVAL, "ensemble member does not fit a full-row tile");
+      const int y_start = (d.n[0] - 1) % by == 0 ? -1 : 0;
+      for (int z0 = 0; z0 < d.n[2]; z0 += b->shape.lz)
+        for (int y0 = y_start; y0 < d.n[0]; y0 += by) items.push_back(make_int4(m, by, y0, z0));
+      continue;
+    }
     const int bx = b->tma ? kTmaBatchBX : kBatchBX;
     const int y_start = (b->tma && (d.n[0] - 1) % b->shape.by == 0) ? -1 : 0;
     for (int z0 = 0; z0 < d.n[2]; z0 += b->shape.lz)
@@ -784,6 +1237,14 @@ lbw_status refresh(lbw_batch* b) {
 template <typename S>
 cudaError_t launch_batch_t(lbw_batch* b, int src) {
   using R = typename Store<S>::R;
+  if constexpr (sizeof(S) >= 4) {
+    if (b->tma && b->shape.by == 0) {
+      batch_row_kernel<S><<<b->blocks, dim3(32, kRowWarps + 1), batch_row_smem<S>(), b->stream>>>(
+          reinterpret_cast<const StepArgs<S>*>(b->members[src]), reinterpret_cast<const CUtensorMap*>(b->maps),
+          src, b->items, b->n_items, b->shape.lz, b->counters, b->nprobe, b->cap);
+      return cudaGetLastError();
+    }
+  }
   if (b->tma) {
     return batch_tma_dispatch<S>(b->shape.by, [&](auto kern, size_t smem) {
       kern<<<b->blocks, dim3(32, b->shape.by + 3), smem, b->stream>>>(
@@ -924,6 +1385,10 @@ lbw_status lbw_batch_create(const lbw_grid_desc* descs, int32_t n, void* stream,
           d.n[1] < 2 * ghost_cols(es) || 7 * ps >= (1LL << 31) || d.n[0] < 2)
         b->tma = false;
     }
+    // full-row tiles: 32- or 64-bit storage and every member's row in a tile
+    b->rowk = b->tma && row_cps(b->prec) > 0;
+    for (int m = 0; m < n && b->rowk; ++m)
+      if (row_tile_rows(descs[m].n[1], es) == 0) b->rowk = false;
   }
   std::vector<double> tab_all;
   size_t ftot = 0;
@@ -1258,8 +1723,10 @@ lbw_status lbw_batch_tune(lbw_batch* b, int32_t trial_steps, const char* cache_p
   std::ostringstream rep;
   if (!cached) {
     // register-pipelined kernel: rows {4, 8, 16} x CTAs per SM {1, 2, 4}; TMA-staged kernel:
-    // rows {4, 7} x CTAs per SM {1, 2}; both x segment planes {16, 32, 64}
+    // rows {4, 7} and full-row tiles (by = 0, where every member fits one) x CTAs per SM
+    // {1, 2}; both x segment planes {16, 32, 64}
     std::vector<int> bys = b->tma ? std::vector<int>{4, 7} : std::vector<int>{4, 8, 16};
+    if (b->rowk) bys.push_back(0);
     std::vector<int> cpss = b->tma ? std::vector<int>{1, 2} : std::vector<int>{1, 2, 4};
     const int lzs[3] = {16, 32, 64};
     cudaEvent_t e0, e1;
@@ -1314,6 +1781,41 @@ lbw_status lbw_batch_tune(lbw_batch* b, int32_t trial_steps, const char* cache_p
     std::strncpy(report, r.c_str(), (size_t)report_cap - 1);
     report[report_cap - 1] = '\0';
   }
+  return LBW_OK;
+}
+
+lbw_status lbw_batch_set_shape(lbw_batch* b, int32_t tile_rows, int32_t seg_planes, int32_t ctas_per_sm) {
+  if (!b) return fail(LBW_EINVAL, "batch is NULL");
+  const bool ok_rows = b->tma ? (tile_rows == 4 || tile_rows == 7 || (tile_rows == 0 && b->rowk))
+                              : (tile_rows == 4 || tile_rows == 8 || tile_rows == 16);
+  if (!ok_rows) return fail(LBW_EINVAL, "tile_rows is not a shape this ensemble's kernel offers");
+  if (seg_planes < 1) return fail(LBW_EINVAL, "seg_planes must be >= 1");
+  const int cps_max = b->tma ? tma_cps(b->prec, tile_rows) : (b->prec == LBW_F32 ? max_cps<float>() : 2);
+  if (ctas_per_sm < 1 || ctas_per_sm > std::max(1, cps_max) || (b->tma && cps_max == 0))
+    return fail(LBW_EINVAL, "ctas_per_sm must be in [1, what the kernel keeps resident]");
+  const Shape old = b->shape;
+  b->shape = Shape{tile_rows, seg_planes, ctas_per_sm};
+  lbw_status st = refresh(b);
+  if (st != LBW_OK) {
+    b->shape = old;
+    refresh(b);
+    return st;
+  }
+  if (b->tma && old.by == 0 && tile_rows != 0) {  // the 64-column kernel reads ghost columns
+    for (int m = 0; m < b->n; ++m) {
+      const Grid& g = b->views[m];
+      const long long rows = 7LL * g.d.n[0] * g.d.n[2];
+      const int blocks = (int)std::min<long long>((rows * 2 * g.col0 + 255) / 256, 1024);
+      prec_dispatch(b->prec, [&](auto tag) {
+        using S = decltype(tag);
+        ghost_fill_kernel<S><<<blocks, 256, 0, b->stream>>>(reinterpret_cast<S*>(g.f[b->cur]), rows, g.pitch,
+                                                             g.d.n[1], g.col0);
+        return 0;
+      });
+    }
+    LBW_CUDA(cudaGetLastError());
+  }
+  LBW_CUDA(cudaStreamSynchronize(b->stream));
   return LBW_OK;
 }
 

@@ -24,7 +24,7 @@ EXPORTS = ["lbw_create_grid", "lbw_init", "lbw_step", "lbw_probe", "lbw_probe_re
            "lbw_set_populations", "lbw_step_count", "lbw_inject_wait_timeout", "lbw_destroy", "lbw_last_error", "lbw_source",
            "lbw_batch_create", "lbw_batch_init", "lbw_batch_probe", "lbw_batch_step", "lbw_batch_source",
            "lbw_batch_probe_read", "lbw_batch_probe_peak", "lbw_batch_spectrum", "lbw_batch_spectrum_lowest", "lbw_batch_get_populations",
-           "lbw_batch_tune", "lbw_batch_info", "lbw_batch_destroy",
+           "lbw_batch_tune", "lbw_batch_set_shape", "lbw_batch_info", "lbw_batch_destroy",
            "lbw_mlp_create", "lbw_mlp_param_count", "lbw_mlp_get_params", "lbw_mlp_set_params",
            "lbw_mlp_forward", "lbw_mlp_predict_bf16", "lbw_mlp_grad", "lbw_mlp_adam_step",
            "lbw_mlp_train", "lbw_mlp_destroy"]
@@ -93,6 +93,7 @@ def lib():
                 "lbw_batch_spectrum_lowest": (st, [vp, i32, ctypes.c_double, dp, dp, ip]),
                 "lbw_batch_get_populations": (st, [vp, i32, dp]),
                 "lbw_batch_tune": (st, [vp, i32, ctypes.c_char_p, ctypes.c_char_p, i32]),
+                "lbw_batch_set_shape": (st, [vp, i32, i32, i32]),
                 "lbw_batch_info": (st, [vp, ctypes.POINTER(i64), ip, ip, ip]),
                 "lbw_batch_destroy": (None, [vp]),
                 "lbw_mlp_create": (st, [i32, i32, i32, i32, ctypes.c_uint64, vp, ctypes.POINTER(vp)]),
@@ -364,6 +365,10 @@ class Batch:
         _check(lib().lbw_batch_tune(self._h, int(trial_steps),
                                     cache_path.encode() if cache_path else None, rep, 8192))
         return rep.value.decode()
+
+    def set_shape(self, tile_rows, seg_planes, ctas_per_sm):
+        """Launch shape chosen by the caller (tile_rows 0: full-row tiles)."""
+        _check(lib().lbw_batch_set_shape(self._h, int(tile_rows), int(seg_planes), int(ctas_per_sm)))
 
     def info(self):
         t, by, lz, cps = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

@@ -170,3 +170,81 @@ def test_lowest_peaks_match_oracle_estimator():
         fo, _ = oracle.spectrum(o.read_probes().sum(0), 5, thresh=1e-2, lowest=True)
         assert cnt[m] == len(fo)
         np.testing.assert_allclose(f[m, : cnt[m]], fo, rtol=1e-8)
+
+
+def _row_members(prec):
+    """Members for full-row tiles: odd and even q2 extents (an odd one ends each row with a
+    phantom node), a narrow row (tiles of 16 rows), a q1 extent whose tiles start at q1 = -1
+    ((n1 - 1) a multiple of the 7 rows of a 64-wide row) and a 100-wide row (3-row tiles)."""
+    from lbw_workloads import ensemble_member, trumpet_params
+    sizes = [(8, 33, 20), (15, 64, 18), (15, 100, 22), (29, 47, 19), (13, 10, 9), (22, 95, 17)]
+    seeds = [200, 201, 202, 203, 204, 305]  # flares the library accepts at c = 0.4
+    return [ensemble_member(n1, n2, n3, *trumpet_params(sd, n1, n3), prec=prec)
+            for (n1, n2, n3), sd in zip(sizes, seeds)]
+
+
+def _ensemble_vs_oracle(b, specs, exc, steps, tol):
+    series = b.read_probes()
+    for m, s in enumerate(specs):
+        o = oracle.OracleGrid(s)
+        o.init(exc[m][0])
+        o.set_probes(exc[m][1], steps)
+        o.step(steps)
+        fo = o.get_f()
+        np.testing.assert_allclose(b.get_f(m), fo, rtol=0, atol=tol * np.abs(fo).max())
+        so = o.read_probes()
+        np.testing.assert_allclose(series[m], so, rtol=0, atol=tol * 10 * np.abs(so).max())
+
+
+@pytest.mark.parametrize("prec,tol", [(PREC_F64, 1e-11), (PREC_F32, 2e-5)], ids=["f64", "f32"])
+def test_full_row_tiles_match_oracle(prec, tol):
+    """The full-row ensemble kernel (tile_rows 0: whole rows per tile, the q2 wrap inside
+    the tile) against the oracle member by member, 120 steps, several q3 segments."""
+    from paper_1705_01801_gb300 import lbw
+    specs = _row_members(prec)
+    exc = [ensemble_excitation(s, sigma=2.5) for s in specs]
+    b = lbw.Batch(specs)
+    try:
+        b.set_shape(0, 8, 2 if prec == PREC_F32 else 1)  # FP64 tiles fill the shared memory of an SM
+        assert b.info()["tile_rows"] == 0
+        b.init([e[0] for e in exc])
+        b.set_probes(np.stack([e[1] for e in exc]), 120)
+        b.step(120)
+        _ensemble_vs_oracle(b, specs, exc, 120, tol)
+    finally:
+        b.close()
+
+
+def test_shape_switch_mid_run_keeps_the_run():
+    """60 steps on full-row tiles, then 60 on 64-column tiles (which read the ghost columns the
+    full-row kernel does not keep; the switch rebuilds them): the same run as the oracle's."""
+    from paper_1705_01801_gb300 import lbw
+    specs = _row_members(PREC_F64)
+    exc = [ensemble_excitation(s, sigma=2.5) for s in specs]
+    b = lbw.Batch(specs)
+    try:
+        b.set_shape(0, 16, 1)
+        b.init([e[0] for e in exc])
+        b.set_probes(np.stack([e[1] for e in exc]), 120)
+        b.step(60)
+        b.set_shape(7, 32, 1)
+        b.step(60)
+        _ensemble_vs_oracle(b, specs, exc, 120, 1e-11)
+    finally:
+        b.close()
+
+
+def test_set_shape_rejects_what_the_ensemble_cannot_run():
+    from paper_1705_01801_gb300 import lbw
+    from lbw_workloads import ensemble_member, trumpet_params
+    wide = [ensemble_member(12, 128, 10, *trumpet_params(5, 12, 10), prec=PREC_F32)]  # 2-row tiles only
+    b = lbw.Batch(wide)
+    try:
+        for shape in ((0, 16, 2), (5, 16, 2), (7, 0, 2), (7, 16, 0), (7, 16, 64)):
+            with pytest.raises(lbw.LbwError) as e:
+                b.set_shape(*shape)
+            assert e.value.status == lbw.LBW_EINVAL
+        b.set_shape(4, 16, 1)
+        assert b.info()["tile_rows"] == 4
+    finally:
+        b.close()
