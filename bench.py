@@ -181,7 +181,12 @@ def run_ensemble(args):
     stream = torch.cuda.Stream()
     sh = lbw.ctypes.c_void_p(stream.cuda_stream)
     b = lbw.Batch(specs, stream=sh)
-    tune_report = b.tune(trial_steps=2).strip().splitlines()[-1]
+    if args.launch:
+        rows, planes, ctas = (int(v) for v in args.launch.split(","))
+        b.set_shape(rows, planes, ctas)
+        tune_report = f"set by={rows} lz={planes} cps={ctas}"
+    else:
+        tune_report = b.tune(trial_steps=2).strip().splitlines()[-1]
     exc = [W.ensemble_excitation(s) for s in specs]
     pulses = [e[0] for e in exc]
     probes_q = np.stack([e[1] for e in exc])
@@ -412,6 +417,9 @@ def main():
                     help="storage override (default: the workload's own)")
     ap.add_argument("--shape", default=None, metavar="N1,N2,N3",
                     help="resize the workload's lattice (smaller profiling captures)")
+    ap.add_argument("--launch", default=None, metavar="ROWS,PLANES,CTAS",
+                    help="ensemble: this launch shape (lbw_batch_set_shape; rows 0 = full-row "
+                         "tiles) instead of the autotuner's")
     ap.add_argument("--geom", default="auto", choices=["auto", "table", "analytic"],
                     help="geometry source of the step kernel (lbw_geom_mode)")
     args = ap.parse_args()
@@ -602,7 +610,7 @@ PROFILES = {
     ("torus", W.PREC_F32): os.path.join(ROOT, "profiles", "step_tma_kernel_torus_192x1024x256_f32.md"),
     ("cylinder", W.PREC_F32): os.path.join(ROOT, "profiles", "step_tma_kernel_cylinder_128x128x256_f32.md"),
 }
-ENSEMBLE_PROFILE = os.path.join(ROOT, "profiles", "batch_tma_kernel_ensemble_32_trumpets_f32.md")
+ENSEMBLE_PROFILE = os.path.join(ROOT, "profiles", "batch_row_kernel_ensemble_32_trumpets_f32.md")
 
 
 def source_hash(name):
