@@ -231,13 +231,15 @@ void lbw_destroy(lbw_grid* g);
  * Ensembles: many independent lattices of uneven sizes (each a full instance of the scheme
  * above with its own geometry and probes) advanced together.  One time step of the whole
  * ensemble is one launch of a persistent kernel over a (member, tile, q3 segment) work list;
- * steps are captured in CUDA graphs.  A member's results are bit-identical to a single lattice
- * run by the register-pipelined step kernel.
+ * steps are captured in CUDA graphs.  A member's results agree with the same lattice run
+ * alone to the rounding of its storage (the kernels may sum in another order).
  * ---------------------------------------------------------------------------------------- */
 typedef struct lbw_batch lbw_batch; /* opaque, library-owned */
 
 /* n members (1..65536), all with the same prec; each descriptor is validated as in
- * lbw_create_grid.  Populations start at zero. */
+ * lbw_create_grid.  Populations start at zero.  The initial launch shape is full-row tiles
+ * with 16-plane segments where every member fits one (see lbw_batch_tune), else 7-row tiles
+ * of 64 columns, else the register-pipelined kernel's default. */
 lbw_status lbw_batch_create(const lbw_grid_desc* descs, int32_t n, void* stream, lbw_batch** out);
 
 /* Initial state at rest for every member: host_counts[m] pulses for member m, taken in order

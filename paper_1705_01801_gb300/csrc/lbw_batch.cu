@@ -1458,7 +1458,11 @@ lbw_status lbw_batch_create(const lbw_grid_desc* descs, int32_t n, void* stream,
     g.table = static_cast<unsigned char*>(b->table) + b->toff[m] * rs;
     g.counters = b->counters;
   }
-  if (b->tma) {
+  if (b->rowk) {  // full-row tiles where every member fits one (the autotuner's pick on trumpets)
+    b->shape.by = 0;
+    b->shape.lz = 16;
+    b->shape.cps = std::min(2, row_cps(b->prec));
+  } else if (b->tma) {
     b->shape.by = 7;
     b->shape.cps = std::min(2, tma_cps(b->prec, 7));
   } else {
