@@ -54,6 +54,28 @@ __global__ void __launch_bounds__(512) step_kernel(const StepArgs<S> a) {
 // Raw post-collision planes are staged in shared memory by the Tensor Memory Accelerator and
 // consumed plane by plane along q3 (see step_tma_kernel).
 
+__host__ __device__ constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+
+// 16-bit storage (whole-plane slots): ONE box per plane holds all seven populations over the
+// BY + 4 rows that the pulls of the BY + 2 consumer rows read (lattice rows y0 - 2 .. y0 + BY
+// + 1, the same rows for every population) and BX + 2V columns (the tile and its 16-byte halo
+// columns, V = 8 elements); a tile on a periodic q2 edge takes its wrapped halo columns (all
+// seven populations) in one more V-column box per wrapped side.  At 16-bit byte rates the
+// per-population boxes (22 copies per plane) bound the kernel by the copies issued, not by
+// the bytes (measured: FP16 trumpet 136 -> 165 GLUPS with the plane box).
+template <int BY, int BX>
+struct PlaneLayout {
+  static constexpr int V = 8, WX = BX + 2 * V, PR = BY + 4;
+  __host__ __device__ static constexpr int row_bytes() { return WX * 2; }
+  __host__ __device__ static constexpr int pop_bytes() { return PR * WX * 2; }
+  __host__ __device__ static constexpr int plane_bytes() { return 7 * pop_bytes(); }
+  __host__ __device__ static constexpr int hpop_bytes() { return PR * 16; }
+  __host__ __device__ static constexpr int halo_bytes() { return 7 * hpop_bytes(); }
+  __host__ __device__ static constexpr int slot_bytes() {
+    return round128(plane_bytes()) + 2 * round128(halo_bytes());
+  }
+};
+
 template <int BY, int BX>
 struct TmaLayout {
   // per population: main box (BY+2) x BX, left / right halo boxes (BY+2) x V, 128-B aligned
@@ -70,21 +92,23 @@ struct TmaLayout {
 // stands for lattice row q1 = y0 - 1 + w (warps 0 and BY + 1 are halo rows; they also compute
 // rho of the tile's two halo columns), lane l owns the NPT nodes q2 = x0 + NPT l ...
 // (BX = 32 NPT columns).  The producer's lane 0 stages raw plane p into slot
-// (p - z0 + 2) mod NB: per
-// population a main box of BX columns x BY + 2 rows (rows shifted by the population's xi1, so
-// the pull of tile row w reads staged row w of every population) and two V-column halo
-// boxes at x0 - V and x0 + BX (periodic wraps in the coordinates), plus the tile's
-// coefficient rows.  With 32- or 64-bit storage a slot holds populations 0-5 of its plane
+// (p - z0 + 2) mod NB: with 32- or 64-bit storage, per population a main box of BX columns x
+// BY + 2 rows (rows shifted by the population's xi1, so the pull of tile row w reads staged
+// row w of every population) and two V-column halo boxes at x0 - V and x0 + BX (periodic
+// wraps in the coordinates); with 16-bit storage the plane box of PlaneLayout (the pull of
+// tile row w reads staged row w + 1 - xi1) and, on a periodic q2 edge, the wrapped halo box;
+// then the tile's coefficient rows.  With 32- or 64-bit storage a slot holds populations 0-5 of its plane
 // and population 6 of the next one (the population that streams down into the plane), so
 // pulling plane u needs the slots of planes u and u - 1 only and the last slot is plane z1;
 // with 16-bit storage a slot holds its whole plane, pulling plane u needs planes u - 1 .. u + 1
-// and the last slot is plane z1 + 1.  The plane below the segment carries population 5 only.
+// and the last slot is plane z1 + 1.  The plane below the segment carries population 5 only
+// (16-bit: its plane box without halo boxes).
 // The slot's full mbarrier completes on the bytes, and a slot is refilled only after every
 // consumer warp has released it (empty mbarrier), so the producer runs up to NB - 2 (16-bit:
-// NB - 3) planes ahead.  Per plane u
-// the consumers pull their populations and write rho into one of three rotating rho planes
-// (step A), synchronise among themselves (named barrier) and collide plane u - 1 (step B,
-// rows of the tile only).  Face rules are reads of other staged values (bounce-back /
+// NB - 3) planes ahead.  Per plane u the consumers read step B's shared inputs of plane
+// u - 1, pull the populations of plane u and write its rho into one of three rotating rho
+// planes (step A), collide plane u - 1 (step B, rows of the tile only), release the slot of
+// plane u - 1 and synchronise among themselves (named barrier).  Face rules are reads of other staged values (bounce-back /
 // anti-bounce-back: the node's own opposite population; free: the node's own population),
 // chosen by selects so the per-plane code has no data-dependent branches; the launch shape
 // keeps halo rows off the q1 faces and halo columns off the q2 faces.  Shared memory is
@@ -102,10 +126,15 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
   constexpr bool RG = sizeof(S) >= 4;
   constexpr int ES = (int)sizeof(S), RS = (int)sizeof(R);
   constexpr int V = 16 / ES;
+  using PL = PlaneLayout<BY, BX>;
+  static_assert(RG || !ANA, "the analytic geometry is built for 32- and 64-bit storage only");
+  // 32/64-bit: per population a main box and two halo boxes; 16-bit: the plane box layout
   constexpr int MB = TmaLayout<BY, BX>::template main_bytes<S>();
   constexpr int HB = TmaLayout<BY, BX>::halo_bytes();
-  constexpr int POPB = TmaLayout<BY, BX>::template pop_bytes<S>();
-  constexpr int SLOTB = TmaLayout<BY, BX>::template slot_bytes<S>();
+  constexpr int POPB = RG ? TmaLayout<BY, BX>::template pop_bytes<S>() : PL::pop_bytes();
+  constexpr int SLOTB = RG ? TmaLayout<BY, BX>::template slot_bytes<S>() : PL::slot_bytes();
+  constexpr int WXB = PL::row_bytes(), HPOP = PL::hpop_bytes();
+  constexpr int HL = round128(PL::plane_bytes()), HR = HL + round128(PL::halo_bytes());
   // rho row: nodes at NPT .. NPT + BX - 1 (vector aligned), halo columns at NPT - 1, NPT + BX
   constexpr int C0 = NPT, PW = BX + 2 * NPT;
   constexpr int PS = ROWS * PW;
@@ -127,6 +156,8 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * a.lz;
   const int z1 = min(z0 + a.lz, a.n3);
   const bool p2 = a.bc[2] == LBW_BC_PERIODIC, p3 = a.bc[4] == LBW_BC_PERIODIC;
+  // 16-bit: the tile's halo column on this side wraps around the periodic q2 axis
+  const bool wrapL = p2 && x0 == 0, wrapR = p2 && x0 + BX == a.n2;
 
   // byte offsets from smem_raw (TMA destinations want 128-byte alignment): barriers, NB
   // slots, three rho planes, NB coefficient blocks
@@ -192,22 +223,19 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
           const unsigned bar = full_at(s);
           const unsigned base = sbase + SL + s * SLOTB;
           const int pg = resolve(p, a.n3, p3);
-          if constexpr (!RG) {  // whole planes
+          if constexpr (!RG) {  // whole planes: the plane box and the wrapped halo boxes
             if (pg < 0) {
               mbar_expect_tx(bar, 0);
-            } else if (p == z0 - 2) {  // only population 5 of this plane streams into the segment
-              mbar_expect_tx(bar, (unsigned)(ROWS * BX * ES));
-              tma_load_4d(base + 5 * POPB, &tm_main, x0, y0 - 1, pg, 5, bar);
             } else {
-              const bool tab = p >= z0 && p < z1;
-              mbar_expect_tx(bar, 7 * tx_pop + (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
-#pragma unroll 1
-              for (int i = 0; i < 7; ++i) {
-                const int row = y0 - 1 - xi1_of(i);
-                tma_load_4d(base + i * POPB, &tm_main, x0, row, pg, i, bar);
-                if (hl) tma_load_4d(base + i * POPB + MB, &tm_halo, xl, row, pg, i, bar);
-                if (hr) tma_load_4d(base + i * POPB + MB + HB, &tm_halo, xr, row, pg, i, bar);
-              }
+              // plane z0 - 2 only gives population 5 at the tile's own columns
+              const bool tab = p >= z0 && p < z1, side = p != z0 - 2;
+              mbar_expect_tx(bar, (unsigned)PL::plane_bytes() +
+                                      (side && wrapL ? (unsigned)PL::halo_bytes() : 0u) +
+                                      (side && wrapR ? (unsigned)PL::halo_bytes() : 0u) +
+                                      (tab ? (unsigned)(BY * T_SLOTS * RS) : 0u));
+              tma_load_4d(base, &tm_main, x0 - PL::V, y0 - 2, pg, 0, bar);
+              if (side && wrapL) tma_load_4d(base + HL, &tm_halo, a.n2 - PL::V, y0 - 2, pg, 0, bar);
+              if (side && wrapR) tma_load_4d(base + HR, &tm_halo, 0, y0 - 2, pg, 0, bar);
               if (tab) tma_load_3d(sbase + TAB + s * TABB, &tm_tab, 0, y0, pg, bar);
             }
           } else if (p == z0 - 2) {
@@ -270,26 +298,7 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
         const unsigned base = sbase + SL + s * SLOTB;
         const int pg = resolve(p, a.n3, p3);
         bool tab = false;  // this plane is collided here: its coefficient rows ride in the slot
-        if constexpr (!RG) {  // whole planes
-          tab = pg >= 0 && p != z0 - 2 && p >= z0 && p < z1;
-          if (lane == 0) {
-            if (pg < 0) {
-              mbar_expect_tx(bar, 0);
-            } else if (p == z0 - 2) {  // only population 5 of this plane streams into the segment
-              mbar_expect_tx(bar, (unsigned)(ROWS * BX * ES));
-              tma_load_4d(base + 5 * POPB, &tm_main, x0, y0 - 1, pg, 5, bar);
-            } else {
-              mbar_expect_tx(bar, 7 * tx_pop + 0u);
-#pragma unroll 1
-              for (int i = 0; i < 7; ++i) {
-                const int row = y0 - 1 - xi1_of(i);
-                tma_load_4d(base + i * POPB, &tm_main, x0, row, pg, i, bar);
-                if (hl) tma_load_4d(base + i * POPB + MB, &tm_halo, xl, row, pg, i, bar);
-                if (hr) tma_load_4d(base + i * POPB + MB + HB, &tm_halo, xr, row, pg, i, bar);
-              }
-            }
-          }
-        } else if (p == z0 - 2) {
+        if (p == z0 - 2) {
           // only population 5 of this plane streams into the segment; when the first pulled
           // plane z0 - 1 is the q3 = 0 face of a wall, its reflected population 6 rides here
           if (lane == 0) {
@@ -370,32 +379,55 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     auto ldv = [&](unsigned off, R (&o)[NPT]) { VecN<S, NPT>::ld(reinterpret_cast<const S*>(smem_raw + off), o); };
     auto ldr = [&](unsigned off) -> R { return *reinterpret_cast<const R*>(smem_raw + off); };
 
-    // offsets within a slot of this lane's vectors: pops 0, 3, 4, 5, 6 at (w, c0); pops 1 / 2
-    // at the pull or at the q1-face rule (the face rows read the staged rows next to them)
-    const unsigned own = (unsigned)(w * BX * ES + c0 * ES);
-    unsigned o1 = POPB + own, o2 = 2 * POPB + own;
+    unsigned own, o1, o2, o3e, o4e;
     R m1 = sc1, m2 = sc1;
-    if (rowin && q1 == 0) {
-      const int b = a.bc[0];
-      if (b == LBW_BC_FREE) o1 = POPB + own + BX * ES;
-      else { o1 = 2 * POPB + own - BX * ES; m1 = sc1 * wall(b); }
+    if constexpr (RG) {
+      // offsets within a slot of this lane's vectors: pops 0, 3, 4, 5, 6 at (w, c0); pops 1 / 2
+      // at the pull or at the q1-face rule (the face rows read the staged rows next to them)
+      own = (unsigned)(w * BX * ES + c0 * ES);
+      o1 = POPB + own;
+      o2 = 2 * POPB + own;
+      if (rowin && q1 == 0) {
+        const int b = a.bc[0];
+        if (b == LBW_BC_FREE) o1 = POPB + own + BX * ES;
+        else { o1 = 2 * POPB + own - BX * ES; m1 = sc1 * wall(b); }
+      }
+      if (rowin && q1 == a.n1 - 1) {
+        const int b = a.bc[1];
+        if (b == LBW_BC_FREE) o2 = 2 * POPB + own - BX * ES;
+        else { o2 = POPB + own + BX * ES; m2 = sc1 * wall(b); }
+      }
+      // pop 3 of node c0 reads column c0 - 1 (left halo box for lane 0), pop 4 of node
+      // c0 + NPT - 1 reads column c0 + NPT (right halo box for lane 31)
+      o3e = lane == 0 ? 3 * POPB + MB + w * 16 + (V - 1) * ES : 3 * POPB + own - ES;
+      o4e = lane == 31 ? 4 * POPB + MB + HB + w * 16 : 4 * POPB + own + NPT * ES;
+    } else {
+      // plane box: lattice row q1 + dr sits in staged row w + 1 + dr of every population,
+      // tile column c at V + c; pop 1 pulls from row q1 - 1, pop 2 from q1 + 1, and the
+      // q1-face rules read the node's own row
+      own = (unsigned)((w + 1) * WXB + (PL::V + c0) * ES);
+      o1 = POPB + own - WXB;
+      o2 = 2 * POPB + own + WXB;
+      if (rowin && q1 == 0) {
+        const int b = a.bc[0];
+        if (b == LBW_BC_FREE) o1 = POPB + own;
+        else { o1 = 2 * POPB + own; m1 = sc1 * wall(b); }
+      }
+      if (rowin && q1 == a.n1 - 1) {
+        const int b = a.bc[1];
+        if (b == LBW_BC_FREE) o2 = 2 * POPB + own;
+        else { o2 = POPB + own; m2 = sc1 * wall(b); }
+      }
+      // columns -1 and BX come from the wrapped halo boxes on a periodic q2 edge
+      o3e = (lane == 0 && wrapL) ? HL + 3 * HPOP + (w + 1) * 16 + (PL::V - 1) * ES : 3 * POPB + own - ES;
+      o4e = (lane == 31 && wrapR) ? HR + 4 * HPOP + (w + 1) * 16 : 4 * POPB + own + NPT * ES;
     }
-    if (rowin && q1 == a.n1 - 1) {
-      const int b = a.bc[1];
-      if (b == LBW_BC_FREE) o2 = 2 * POPB + own - BX * ES;
-      else { o2 = POPB + own + BX * ES; m2 = sc1 * wall(b); }
-    }
-    // pop 3 of node c0 reads column c0 - 1 (left halo box for lane 0), pop 4 of node
-    // c0 + NPT - 1 reads column c0 + NPT (right halo box for lane 31)
-    const unsigned o3e = lane == 0 ? 3 * POPB + MB + w * 16 + (V - 1) * ES : 3 * POPB + own - ES;
-    const unsigned o4e = lane == 31 ? 4 * POPB + MB + HB + w * 16 : 4 * POPB + own + NPT * ES;
     // q2 faces (non-periodic q2): free copies the node's own value, walls reflect the opposite
     const bool q2lo_free = a.bc[2] == LBW_BC_FREE, q2hi_free = a.bc[3] == LBW_BC_FREE;
     const R q2lo_m = sc1 * wall(a.bc[2]), q2hi_m = sc1 * wall(a.bc[3]);
     // q3 faces: populations 5 / 6 at the first / last plane take the node's own value (free)
     // or its opposite population (walls), with these factors
     const bool f5_own = a.bc[4] == LBW_BC_FREE, f6_own = a.bc[5] == LBW_BC_FREE;
-    const unsigned f5_face = (f5_own ? 5 : 6) * POPB, f6_face = (f6_own ? 6 : 5) * POPB;
     const R m5_face = a.bc[4] == LBW_BC_FREE ? sc1 : sc1 * wall(a.bc[4]);
     const R m6_face = a.bc[5] == LBW_BC_FREE ? sc1 : sc1 * wall(a.bc[5]);
 
@@ -407,8 +439,37 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
     const bool hcol = hwarp && lane < BY;
     const bool hin = hq1 < a.n1 && (p2 || (hq2 >= 0 && hq2 < a.n2));
     unsigned h0, h1, h2, h3, h4;
+    unsigned hps = POPB;  // population stride at the halo column node
     R hm1 = sc1, hm2 = sc1;
-    {
+    if constexpr (!RG) {
+      // plane box: lattice row y0 + hl is staged row hl + 2; the column node lies in a
+      // wrapped halo box on a periodic q2 edge, else in the plane box
+      const int hr2 = hl + 2;
+      const bool hh = (w == 0) ? wrapL : wrapR;
+      hps = hh ? HPOP : POPB;
+      auto hat = [&](int pop, int r) -> unsigned {
+        return hh ? (unsigned)(((w == 0) ? HL : HR) + pop * HPOP + r * 16 + ((w == 0) ? (PL::V - 1) * ES : 0))
+                  : (unsigned)(pop * POPB + r * WXB + (PL::V + ((w == 0) ? -1 : BX)) * ES);
+      };
+      h0 = hat(0, hr2);
+      h1 = hat(1, hr2 - 1);
+      h2 = hat(2, hr2 + 1);
+      // pop 3 from column -2 / BX - 1, pop 4 from column 0 / BX + 1
+      h3 = (w == 0) ? (wrapL ? HL + 3 * HPOP + hr2 * 16 + (PL::V - 2) * ES : 3 * POPB + hr2 * WXB + (PL::V - 2) * ES)
+                    : 3 * POPB + hr2 * WXB + (PL::V + BX - 1) * ES;
+      h4 = (w == 0) ? 4 * POPB + hr2 * WXB + PL::V * ES
+                    : (wrapR ? HR + 4 * HPOP + hr2 * 16 + ES : 4 * POPB + hr2 * WXB + (PL::V + BX + 1) * ES);
+      if (hq1 == 0) {
+        const int b = a.bc[0];
+        if (b == LBW_BC_FREE) h1 = hat(1, hr2);
+        else { h1 = hat(2, hr2); hm1 = sc1 * wall(b); }
+      }
+      if (hq1 == a.n1 - 1) {
+        const int b = a.bc[1];
+        if (b == LBW_BC_FREE) h2 = hat(2, hr2);
+        else { h2 = hat(1, hr2); hm2 = sc1 * wall(b); }
+      }
+    } else {
       const int hw = hl + 1;
       // column -1 lives in the left halo box (index V - 1), column BX in the right one (0)
       const unsigned hbox = (w == 0) ? MB : MB + HB, hcolb = (w == 0) ? (V - 1) * ES : 0;
@@ -452,13 +513,19 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       const bool zlo = !p3 && u == 0, zhi = !p3 && u == a.n3 - 1;
       const bool zghost = !p3 && (u < 0 || u >= a.n3);
       const unsigned S0 = SL + sl0 * SLOTB, SM = SL + slm * SLOTB;
-      unsigned B5, B6;
+      unsigned B5, B6, H5, H6;
       if constexpr (RG) {
         B5 = zlo ? (f5_own ? S0 + 5 * POPB : SM + 6 * POPB) : SM + 5 * POPB;
         B6 = zhi ? (f6_own ? SM + 6 * POPB : S0 + 5 * POPB) : S0 + 6 * POPB;
+        H5 = B5;
+        H6 = B6;
       } else {
-        B5 = zlo ? S0 + f5_face : SM + 5 * POPB;
-        B6 = zhi ? S0 + f6_face : SL + slp * SLOTB + 6 * POPB;
+        const unsigned s5 = zlo ? S0 : SM, s6 = zhi ? S0 : SL + slp * SLOTB;
+        const int p5 = zlo ? (f5_own ? 5 : 6) : 5, p6 = zhi ? (f6_own ? 6 : 5) : 6;
+        B5 = s5 + p5 * POPB;
+        B6 = s6 + p6 * POPB;
+        H5 = s5 + p5 * hps;
+        H6 = s6 + p6 * hps;
       }
       const R m5 = zlo ? m5_face : sc1, m6 = zhi ? m6_face : sc1;
       R t3[NPT], t4[NPT];
@@ -522,8 +589,8 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
           g[2] = hm2 * ld1(S0 + h2);
           g[3] = sc1 * ld1(S0 + h3);
           g[4] = sc1 * ld1(S0 + h4);
-          g[5] = m5 * ld1(B5 + h0);  // h0 addresses population 0: B5 / B6 add their own
-          g[6] = m6 * ld1(B6 + h0);
+          g[5] = m5 * ld1(H5 + h0);  // h0 addresses population 0: H5 / H6 add their own
+          g[6] = m6 * ld1(H6 + h0);
           const R h = SC ? a.w[0] * g[0] + a.w[1] * (((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]))
                          : ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
           if (hcol) *reinterpret_cast<R*>(smem_raw + pl + hrho) = (hin && !zghost) ? h : R(0);
@@ -531,23 +598,29 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
       }
     };
 
-    // step B: collide plane zc with populations fc, rho (rp, rc, rn)
-    auto stepB = [&](int zc, R (&fc)[7][NPT], const R (&rp)[NPT], const R (&rc)[NPT],
-                     const R (&rn)[NPT], int slz, int rbz) {
+    // step B's shared-memory inputs for plane zc: rho of plane zc at the neighbours in q1 and
+    // q2 (rho plane rbz) and the tile row's coefficients (slot slz).  They are read before
+    // step A of the plane ahead, which writes another rho plane, so their latency overlaps
+    // with step A's work.
+    struct BIn {
+      R ru[NPT], rd[NPT], lft, rgt;
+      int slz;
+    };
+    auto loadB = [&](BIn& b, int slz, int rbz) {
       const unsigned cur = RHO + rbz * (PS * RS) + myrho;
-      R ru[NPT], rd[NPT];
-      VecN<R, NPT>::ld(reinterpret_cast<const R*>(smem_raw + cur + PW * RS), ru);
-      VecN<R, NPT>::ld(reinterpret_cast<const R*>(smem_raw + cur - PW * RS), rd);
-      const R lft = ldr(cur - RS), rgt = ldr(cur + NPT * RS);
-      R rl[NPT], rrt[NPT];
-      rl[0] = q2lo ? a.s2lo * rc[0] : lft;
-      rrt[NPT - 1] = q2hi ? a.s2hi * rc[NPT - 1] : rgt;
-#pragma unroll
-      for (int k = 0; k + 1 < NPT; ++k) {
-        rl[k + 1] = rc[k];
-        rrt[k] = rc[k + 1];
-      }
-      const unsigned T = TAB + slz * TABB + (w - 1) * (T_SLOTS * RS);
+      VecN<R, NPT>::ld(reinterpret_cast<const R*>(smem_raw + cur + PW * RS), b.ru);
+      VecN<R, NPT>::ld(reinterpret_cast<const R*>(smem_raw + cur - PW * RS), b.rd);
+      b.lft = ldr(cur - RS);
+      b.rgt = ldr(cur + NPT * RS);
+      b.slz = slz;
+    };
+
+    // step B: collide plane zc with populations fc, rho (rp, rc, rn) and the inputs in bi
+    auto stepB = [&](int zc, R (&fc)[7][NPT], const R (&rp)[NPT], const R (&rc)[NPT],
+                     const R (&rn)[NPT], const BIn& bi) {
+      const R (&ru)[NPT] = bi.ru;
+      const R (&rd)[NPT] = bi.rd;
+      const unsigned T = TAB + bi.slz * TABB + (w - 1) * (T_SLOTS * RS);
       R c[T_SLOTS];
 #pragma unroll
       for (int k = 0; k < T_SLOTS; k += 4) {
@@ -559,6 +632,14 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
           const double2 v1 = *reinterpret_cast<const double2*>(smem_raw + T + (k + 2) * RS);
           c[k] = v0.x; c[k + 1] = v0.y; c[k + 2] = v1.x; c[k + 3] = v1.y;
         }
+      }
+      R rl[NPT], rrt[NPT];
+      rl[0] = q2lo ? a.s2lo * rc[0] : bi.lft;
+      rrt[NPT - 1] = q2hi ? a.s2hi * rc[NPT - 1] : bi.rgt;
+#pragma unroll
+      for (int k = 0; k + 1 < NPT; ++k) {
+        rl[k + 1] = rc[k];
+        rrt[k] = rc[k + 1];
       }
       if constexpr (sizeof(R) == 4) {
         // node pairs (k, k + 1) in paired FP32 instructions; negated coefficients give -D1 and
@@ -674,17 +755,24 @@ __global__ void __launch_bounds__(32 * (BY + 3)) step_tma_kernel(
         s2 = s2 == NB - 1 ? 0 : s2 + 1;
         if ((RG ? s1 : s2) == 0) ++uw;
       };
-      // iteration z: raw plane z + 1 (RG) or z + 2 in, A(z + 1), barrier, B(z), release raw
-      // plane z.  Every warp passes the same barriers; the barrier ORs the warps' abort states
-      // (a timed-out wait here, or the producer's flag), so all warps leave after the same
-      // iteration.
+      // iteration z: raw plane z + 1 (RG) or z + 2 in, B(z)'s shared-memory reads, A(z + 1),
+      // B(z), release raw plane z, barrier.  B(z) needs rho of plane z + 1 only at the warp's
+      // own nodes (its own A(z + 1)) and rho plane z, which every warp wrote before the previous
+      // iteration's barrier; A(z + 1) writes rho plane z + 1, whose buffer was last read by
+      // B(z - 2), two barriers back.  Every warp passes the same barriers; the barrier ORs the
+      // warps' abort states (a timed-out wait here, or the producer's flag), so all warps leave
+      // after the same iteration.
       auto iter = [&](int zz, R (&fc)[7][NPT], R (&fn)[7][NPT], const R (&rp)[NPT],
                       const R (&rc)[NPT], R (&rn)[NPT], bool collide) {
         const bool in = wait_bar(full_at(RG ? s1 : s2), (unsigned)(uw & 1));
-        if (in) stepA(zz + 1, fn, rn, sz, s1, s2, rb1, true);
-        const bool go = !named_sync_or(1, NCW * 32, !in || abort_flag);
-        if (go && collide) stepB(zz, fc, rp, rc, rn, sz, rbz);
+        if (in) {
+          BIn bi;
+          if (collide) loadB(bi, sz, rbz);
+          stepA(zz + 1, fn, rn, sz, s1, s2, rb1, true);
+          if (collide) stepB(zz, fc, rp, rc, rn, bi);
+        }
         if (lane == 0) mbar_arrive(empty_at(sz));  // raw plane zz is no longer needed
+        const bool go = !named_sync_or(1, NCW * 32, !in || abort_flag);
         advance();
         return go;
       };
@@ -774,8 +862,9 @@ constexpr size_t tma_smem_bytes() {
   using R = typename Store<S>::R;
   constexpr int BX = 32 * NPT, NB = 5, PS = (BY + 2) * (BX + 2 * NPT);
   constexpr int TABB = ((BY * T_SLOTS * (int)sizeof(R)) + 127) / 128 * 128;
-  return 128 /* alignment slack */ + 128 /* barriers */ +
-         (size_t)NB * TmaLayout<BY, BX>::template slot_bytes<S>() +
+  constexpr int SLOTB = sizeof(S) == 2 ? PlaneLayout<BY, BX>::slot_bytes()
+                                       : TmaLayout<BY, BX>::template slot_bytes<S>();
+  return 128 /* alignment slack */ + 128 /* barriers */ + (size_t)NB * SLOTB +
          ((3 * PS * sizeof(R) + 127) / 128) * 128 + (size_t)NB * TABB +
          (ANA ? ((3 * (BY + 2) * sizeof(MetricR<R>) + 127) / 128) * 128 : 0);  // see step_tma_kernel
 }
@@ -892,8 +981,13 @@ bool build_tmaps(Grid* g, int by, int bx) {
   const cuuint64_t strides[3] = {(cuuint64_t)g->d.n[1] * es, (cuuint64_t)g->d.n[1] * g->d.n[0] * es,
                                  (cuuint64_t)g->nn * es};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const cuuint32_t box_main[4] = {(cuuint32_t)bx, (cuuint32_t)(by + 2), 1, 1};
-  const cuuint32_t box_halo[4] = {(cuuint32_t)(16 / es), (cuuint32_t)(by + 2), 1, 1};
+  // 32/64-bit: one population's main (bx x BY+2) and halo (V x BY+2) boxes; 16-bit: the plane
+  // box (bx + 2V x BY+4, all seven populations) and the wrapped halo box (V x BY+4, seven)
+  const bool plane = es == 2;
+  const cuuint32_t box_main[4] = {(cuuint32_t)(plane ? bx + 2 * (16 / es) : bx),
+                                  (cuuint32_t)(by + (plane ? 4 : 2)), 1, plane ? 7u : 1u};
+  const cuuint32_t box_halo[4] = {(cuuint32_t)(16 / es), (cuuint32_t)(by + (plane ? 4 : 2)), 1,
+                                  plane ? 7u : 1u};
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(g->tmaps);
   for (int b = 0; b < 2; ++b) {
     if (encode(&m[2 * b], dt, 4, g->f[b], dims, strides, box_main, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
