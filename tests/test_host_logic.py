@@ -67,3 +67,21 @@ def test_profiled_traffic_follows_the_kernel_source(monkeypatch):
     assert bench.profiled_traffic("cylinder", spec) is None
     assert bench.profiled_ensemble_traffic(1000) is None
 
+
+
+def test_committed_profiles_match_the_kernel_sources():
+    """The committed ncu summaries were taken on the kernel sources as they stand, so the
+    benchmark lines of the torus (the headline), the cylinder and the ensemble carry measured
+    DRAM traffic; a kernel edit without retaken counters fails here."""
+    import bench
+    import lbw_workloads as W
+    for name in ("torus", "cylinder"):
+        spec = W.workload(name).spec
+        fields = bench._profile_fields(bench.PROFILES[(name, W.PREC_F32)])
+        assert fields["step_source_sha256_16"] == bench.lbw_kernel_hash(), name
+        traffic = bench.profiled_traffic(name, spec)
+        assert traffic == int(fields["traffic_bytes_per_launch"])
+        # within a few percent of the 56 B per node that one launch moves at least in part
+        assert 0.75 < traffic / (56 * spec.nodes) < 1.1, (name, traffic)
+    ens = bench._profile_fields(bench.ENSEMBLE_PROFILE)
+    assert ens["batch_source_sha256_16"] == bench.source_hash("lbw_batch.cu")
